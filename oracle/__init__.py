@@ -1,0 +1,251 @@
+"""CPU oracle for FAMSA stages I+II -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+arms of ``bench.py`` may import this package.  The GPU library never calls
+it, and it imports nothing from the GPU package: the two share no code.
+
+``oracle.c`` holds the arithmetic (plain C, OpenMP over independent pairs
+only); this module compiles it with gcc and wraps it with numpy.
+
+Functions and the paper passages they follow (FAMSA, Methods):
+
+* :func:`lcs`, :func:`lcs_pairs`, :func:`lcs_allpairs`, :func:`lcs_rows` --
+  LCS length by the textbook DP rule ("Pairwise similarities calculation").
+* :func:`key` -- the exact rational distance indel^2 / LCS used to order
+  pairs; indel = |A| + |B| - 2 LCS and similarity = LCS / indel^2 are the
+  two displayed equations of the same subsection.
+* :func:`slink_matrix`, :func:`slink_streamed` -- Sibson's SLINK pointer
+  representation ("Determination of the guide tree").
+* :func:`slink_naive` -- naive single-linkage agglomeration, then the
+  pointer representation read off the merges.
+* :func:`slink_definition` -- the pointer representation evaluated from its
+  definition via the minimax (single-link ultrametric) closure.
+* :func:`merges` -- the merge list with the fixed (lambda, index) order.
+
+Every function here is pinned by ``tests/test_oracle_*.py`` against brute
+force, closed forms, invariants, textbook examples or library routines.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2 -fopenmp, no SIMD intrinsics)."""
+    with _lock:
+        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+            cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC]
+            try:
+                subprocess.check_call(cmd)
+            except subprocess.CalledProcessError:
+                subprocess.check_call([c for c in cmd if c != "-fopenmp"])
+            os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i32, i64, u64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32
+        sig = {
+            "oracle_key_cmp": ([u64, u32, u64, u32], ctypes.c_int),
+            "oracle_lcs": ([_P, i32, _P, i32], i32),
+            "oracle_num_threads": ([], ctypes.c_int),
+            "oracle_lcs_pairs": ([_P, _P, i32, _P, _P, i64, _P, ctypes.c_int], ctypes.c_int),
+            "oracle_lcs_allpairs": ([_P, _P, i32, _P, ctypes.c_int], ctypes.c_int),
+            "oracle_lcs_rows": ([_P, _P, i32, i32, i32, _P, ctypes.c_int], ctypes.c_int),
+            "oracle_slink_matrix": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
+            "oracle_slink_streamed": ([_P, _P, i32, _P, _P, _P, ctypes.c_int], ctypes.c_int),
+            "oracle_slink_naive": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
+            "oracle_slink_definition": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
+            "oracle_minimax": ([_P, _P, i32, _P, _P], ctypes.c_int),
+            "oracle_merges": ([_P, _P, _P, i32, _P, _P, _P, _P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError("%s failed with code %d" % (what, rc))
+
+
+def _prep(residues, offsets):
+    res = np.ascontiguousarray(residues, dtype=np.uint8)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    return res, off, len(off) - 1
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+# --------------------------------------------------------------------- LCS
+def lcs(a, b) -> int:
+    """LCS length of two code sequences by the DP rule."""
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    b = np.ascontiguousarray(b, dtype=np.uint8)
+    r = _load().oracle_lcs(_ptr(a), len(a), _ptr(b), len(b))
+    _check(0 if r >= 0 else r, "oracle_lcs")
+    return int(r)
+
+
+def lcs_pairs(residues, offsets, pa, pb, nthreads: int = 0) -> np.ndarray:
+    res, off, k = _prep(residues, offsets)
+    pa = np.ascontiguousarray(pa, dtype=np.int32)
+    pb = np.ascontiguousarray(pb, dtype=np.int32)
+    out = np.empty(len(pa), dtype=np.int32)
+    _check(_load().oracle_lcs_pairs(_ptr(res), _ptr(off), k, _ptr(pa), _ptr(pb), len(pa),
+                                    _ptr(out), nthreads), "oracle_lcs_pairs")
+    return out
+
+
+def lcs_allpairs(residues, offsets, nthreads: int = 0) -> np.ndarray:
+    """LCS of all pairs i < j, row-major (length k(k-1)/2)."""
+    res, off, k = _prep(residues, offsets)
+    out = np.empty(k * (k - 1) // 2, dtype=np.int32)
+    _check(_load().oracle_lcs_allpairs(_ptr(res), _ptr(off), k, _ptr(out), nthreads),
+           "oracle_lcs_allpairs")
+    return out
+
+
+def lcs_rows(residues, offsets, r0: int, r1: int, nthreads: int = 0) -> np.ndarray:
+    """Rows r0..r1-1 of the lower triangle: row i lists LCS(i, j) for j = 0..i-1."""
+    res, off, k = _prep(residues, offsets)
+    n = (r1 * (r1 - 1) - r0 * (r0 - 1)) // 2
+    out = np.empty(n, dtype=np.int32)
+    _check(_load().oracle_lcs_rows(_ptr(res), _ptr(off), k, r0, r1, _ptr(out), nthreads),
+           "oracle_lcs_rows")
+    return out
+
+
+def tri_to_square(tri: np.ndarray, k: int, diag=0) -> np.ndarray:
+    m = np.full((k, k), diag, dtype=tri.dtype)
+    iu = np.triu_indices(k, 1)
+    m[iu] = tri
+    m[(iu[1], iu[0])] = tri
+    return m
+
+
+# --------------------------------------------------------------------- keys
+def key(lcs_len: int, la: int, lb: int):
+    """Exact distance indel^2 / LCS as an unreduced (num, den); den 0 = +inf."""
+    indel = la + lb - 2 * lcs_len
+    if lcs_len == 0:
+        return (1, 0)
+    return (indel * indel, lcs_len)
+
+
+def key_cmp(a, b) -> int:
+    r = _load().oracle_key_cmp(a[0], a[1], b[0], b[1])
+    if r == -2:
+        raise ValueError("0/0 is not a key")
+    return int(r)
+
+
+# --------------------------------------------------------------------- trees
+def _tree_out(k):
+    return (np.empty(k, dtype=np.int32), np.empty(k, dtype=np.uint64), np.empty(k, dtype=np.uint32))
+
+
+def _lens(offsets):
+    return np.ascontiguousarray(np.diff(np.asarray(offsets, dtype=np.int64)), dtype=np.int32)
+
+
+def slink_matrix(lcs_tri, lens):
+    """Sibson's SLINK over a precomputed triangle; returns (pi, lambda_num, lambda_den)."""
+    tri = np.ascontiguousarray(lcs_tri, dtype=np.int32)
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    k = len(lens)
+    pi, ln, ld = _tree_out(k)
+    _check(_load().oracle_slink_matrix(_ptr(tri), _ptr(lens), k, _ptr(pi), _ptr(ln), _ptr(ld)),
+           "oracle_slink_matrix")
+    return pi, ln, ld
+
+
+def slink_streamed(residues, offsets, nthreads: int = 0):
+    """SLINK with row n computed by DP when point n is inserted (no k x k storage)."""
+    res, off, k = _prep(residues, offsets)
+    pi, ln, ld = _tree_out(k)
+    _check(_load().oracle_slink_streamed(_ptr(res), _ptr(off), k, _ptr(pi), _ptr(ln), _ptr(ld),
+                                         nthreads), "oracle_slink_streamed")
+    return pi, ln, ld
+
+
+def slink_naive(lcs_tri, lens):
+    tri = np.ascontiguousarray(lcs_tri, dtype=np.int32)
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    k = len(lens)
+    pi, ln, ld = _tree_out(k)
+    _check(_load().oracle_slink_naive(_ptr(tri), _ptr(lens), k, _ptr(pi), _ptr(ln), _ptr(ld)),
+           "oracle_slink_naive")
+    return pi, ln, ld
+
+
+def slink_definition(lcs_tri, lens):
+    tri = np.ascontiguousarray(lcs_tri, dtype=np.int32)
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    k = len(lens)
+    pi, ln, ld = _tree_out(k)
+    _check(_load().oracle_slink_definition(_ptr(tri), _ptr(lens), k, _ptr(pi), _ptr(ln),
+                                           _ptr(ld)), "oracle_slink_definition")
+    return pi, ln, ld
+
+
+def minimax(lcs_tri, lens):
+    """Single-link ultrametric u (k x k) as reduced (num, den) arrays."""
+    tri = np.ascontiguousarray(lcs_tri, dtype=np.int32)
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    k = len(lens)
+    un = np.empty((k, k), dtype=np.uint64)
+    ud = np.empty((k, k), dtype=np.uint32)
+    _check(_load().oracle_minimax(_ptr(tri), _ptr(lens), k, _ptr(un), _ptr(ud)), "oracle_minimax")
+    return un, ud
+
+
+def merges(pi, lnum, lden):
+    """Merge list: (pairs int32[k-1,2], h_num, h_den, sizes)."""
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    lnum = np.ascontiguousarray(lnum, dtype=np.uint64)
+    lden = np.ascontiguousarray(lden, dtype=np.uint32)
+    k = len(pi)
+    m = max(k - 1, 0)
+    pairs = np.empty((m, 2), dtype=np.int32)
+    hn = np.empty(m, dtype=np.uint64)
+    hd = np.empty(m, dtype=np.uint32)
+    sz = np.empty(m, dtype=np.int32)
+    _check(_load().oracle_merges(_ptr(pi), _ptr(lnum), _ptr(lden), k, _ptr(pairs), _ptr(hn),
+                                 _ptr(hd), _ptr(sz)), "oracle_merges")
+    return pairs, hn, hd, sz
+
+
+def tree(residues, offsets, nthreads: int = 0):
+    """Full oracle result for a family: dict with pi, lambda, merges (streamed SLINK)."""
+    pi, ln, ld = slink_streamed(residues, offsets, nthreads)
+    pairs, hn, hd, sz = merges(pi, ln, ld)
+    return {"pi": pi, "lambda_num": ln, "lambda_den": ld, "merges": pairs, "h_num": hn,
+            "h_den": hd, "sizes": sz}

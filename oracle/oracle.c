@@ -1,0 +1,509 @@
+/*
+ * CPU oracle for FAMSA stages I+II (test infrastructure only).
+ *
+ * Plain, slow, obviously correct restatements of what the GPU path computes.
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline arm
+ * may load this library; the product path never does.  It shares no code,
+ * header, table or helper with the CUDA library.
+ *
+ * What it computes (citations are to the FAMSA paper, Methods):
+ *   - LCS length by the textbook dynamic-programming rule ("Pairwise
+ *     similarities calculation": the LCS length is the maximal number of
+ *     perfectly matching columns, computable by a straightforward DP rule).
+ *     Matching is literal code equality (ambiguity codes match only
+ *     themselves).
+ *   - indel(A,B) = |A| + |B| - 2 LCS(A,B) and similarity = LCS / indel^2
+ *     (the two displayed equations of that subsection).  The tree is keyed on
+ *     the exact rational distance indel^2 / LCS, a strictly decreasing
+ *     transform of the similarity; LCS = 0 gives +infinity, indel = 0 gives 0.
+ *     Keys are compared by 128-bit cross multiplication, never in floating
+ *     point.
+ *   - single-linkage guide tree ("Determination of the guide tree") in
+ *     Sibson's pointer representation (pi, lambda), three independent ways:
+ *       (i)   Sibson's SLINK insertion, one point at a time in index order;
+ *       (ii)  naive agglomeration: repeatedly merge the closest two clusters
+ *             with the single-link update min(d(A,C), d(B,C));
+ *       (iii) the definition: minimax (bottleneck) path distances by a
+ *             Floyd-Warshall closure, then lambda(j) = min_{l>j} u(j,l) and
+ *             pi(j) = max{ l > j : u(j,l) <= lambda(j) }.
+ *   - merge list: indices sorted by (lambda, index) ascending, then
+ *     union-find over (j, pi(j)) at height lambda(j); new cluster ids k+t.
+ *
+ * All functions return 0 on success and a negative value on bad arguments
+ * or allocation failure.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------ keys */
+typedef struct { uint64_t num; uint32_t den; } okey; /* num/den, den == 0 means +inf */
+
+static okey key_from_lcs(int32_t lcs, int32_t la, int32_t lb) {
+  okey k;
+  uint64_t indel = (uint64_t)(la + lb - 2 * lcs);
+  k.num = indel * indel;
+  k.den = (uint32_t)lcs;
+  if (k.den == 0) k.num = 1; /* +inf, canonical */
+  return k;
+}
+static const okey KEY_INF = {1, 0};
+
+/* a < b */
+static int key_lt(okey a, okey b) {
+  if (a.den == 0) return 0;
+  if (b.den == 0) return 1;
+  return (u128)a.num * b.den < (u128)b.num * a.den;
+}
+static okey key_min(okey a, okey b) { return key_lt(b, a) ? b : a; }
+static okey key_max(okey a, okey b) { return key_lt(a, b) ? b : a; }
+
+static uint64_t gcd64(uint64_t a, uint64_t b) {
+  while (b) { uint64_t t = a % b; a = b; b = t; }
+  return a;
+}
+static void key_reduce(okey k, uint64_t *num, uint32_t *den) {
+  if (k.den == 0) { *num = 1; *den = 0; return; }
+  if (k.num == 0) { *num = 0; *den = 1; return; }
+  uint64_t g = gcd64(k.num, k.den);
+  *num = k.num / g;
+  *den = (uint32_t)(k.den / g);
+}
+
+/* exposed for the comparator tests: returns -1, 0, 1 */
+int oracle_key_cmp(uint64_t an, uint32_t ad, uint64_t bn, uint32_t bd) {
+  okey a = {an, ad}, b = {bn, bd};
+  if (a.den == 0 && a.num == 0) return -2;
+  if (b.den == 0 && b.num == 0) return -2;
+  if (key_lt(a, b)) return -1;
+  if (key_lt(b, a)) return 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------ LCS by DP */
+/* L[i][j] = L[i-1][j-1] + 1 if a_i == b_j else max(L[i-1][j], L[i][j-1]); two rows. */
+static int32_t lcs_dp(const uint8_t *a, int32_t la, const uint8_t *b, int32_t lb, int32_t *row) {
+  for (int32_t j = 0; j <= lb; ++j) row[j] = 0;
+  for (int32_t i = 1; i <= la; ++i) {
+    int32_t diag = 0; /* L[i-1][j-1] */
+    for (int32_t j = 1; j <= lb; ++j) {
+      int32_t up = row[j];      /* L[i-1][j] */
+      int32_t left = row[j - 1]; /* L[i][j-1] (already overwritten) */
+      int32_t v;
+      if (a[i - 1] == b[j - 1]) v = diag + 1;
+      else v = up > left ? up : left;
+      diag = up;
+      row[j] = v;
+    }
+  }
+  return row[lb];
+}
+
+int32_t oracle_lcs(const uint8_t *a, int32_t la, const uint8_t *b, int32_t lb) {
+  if (la < 0 || lb < 0) return -1;
+  int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(lb + 1));
+  if (!row) return -2;
+  int32_t r = lcs_dp(a, la, b, lb, row);
+  free(row);
+  return r;
+}
+
+static int32_t max_len(const int64_t *off, int32_t k) {
+  int32_t m = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    int32_t l = (int32_t)(off[i + 1] - off[i]);
+    if (l > m) m = l;
+  }
+  return m;
+}
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* LCS for an explicit list of pairs (pa[t], pb[t]) */
+int oracle_lcs_pairs(const uint8_t *res, const int64_t *off, int32_t k, const int32_t *pa,
+                     const int32_t *pb, int64_t npairs, int32_t *out, int nthreads) {
+  if (k < 1 || npairs < 0) return -1;
+  set_threads(nthreads);
+  int32_t ml = max_len(off, k);
+  int bad = 0;
+#pragma omp parallel
+  {
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ml + 1));
+    if (!row) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t t = 0; t < npairs; ++t) {
+      if (!row) continue;
+      int32_t i = pa[t], j = pb[t];
+      out[t] = lcs_dp(res + off[i], (int32_t)(off[i + 1] - off[i]), res + off[j],
+                      (int32_t)(off[j + 1] - off[j]), row);
+    }
+    free(row);
+  }
+  return bad ? -2 : 0;
+}
+
+/* all pairs i < j, row-major: index(i,j) = i*k - i*(i+1)/2 + (j - i - 1) */
+int oracle_lcs_allpairs(const uint8_t *res, const int64_t *off, int32_t k, int32_t *out,
+                        int nthreads) {
+  if (k < 1) return -1;
+  set_threads(nthreads);
+  int32_t ml = max_len(off, k);
+  int bad = 0;
+#pragma omp parallel
+  {
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ml + 1));
+    if (!row) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = 0; i < k; ++i) {
+      if (!row) continue;
+      int64_t base = (int64_t)i * k - (int64_t)i * (i + 1) / 2;
+      for (int32_t j = i + 1; j < k; ++j)
+        out[base + (j - i - 1)] = lcs_dp(res + off[i], (int32_t)(off[i + 1] - off[i]),
+                                         res + off[j], (int32_t)(off[j + 1] - off[j]), row);
+    }
+    free(row);
+  }
+  return bad ? -2 : 0;
+}
+
+/* LCS rows: for i in [r0, r1), j in [0, i): out[(sum_{r0<=i'<i} i') + j] */
+int oracle_lcs_rows(const uint8_t *res, const int64_t *off, int32_t k, int32_t r0, int32_t r1,
+                    int32_t *out, int nthreads) {
+  if (k < 1 || r0 < 0 || r1 > k || r0 > r1) return -1;
+  set_threads(nthreads);
+  int32_t ml = max_len(off, k);
+  int bad = 0;
+#pragma omp parallel
+  {
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ml + 1));
+    if (!row) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = r0; i < r1; ++i) {
+      if (!row) continue;
+      int64_t base = ((int64_t)i * (i - 1) - (int64_t)r0 * (r0 - 1)) / 2;
+      for (int32_t j = 0; j < i; ++j)
+        out[base + j] = lcs_dp(res + off[i], (int32_t)(off[i + 1] - off[i]), res + off[j],
+                               (int32_t)(off[j + 1] - off[j]), row);
+    }
+    free(row);
+  }
+  return bad ? -2 : 0;
+}
+
+/* ------------------------------------------------------------ trees */
+static int64_t tri_index(int32_t i, int32_t j, int32_t k) { /* i < j */
+  return (int64_t)i * k - (int64_t)i * (i + 1) / 2 + (j - i - 1);
+}
+static okey tri_key(const int32_t *lcs_tri, const int32_t *lens, int32_t k, int32_t i, int32_t j) {
+  if (i > j) { int32_t t = i; i = j; j = t; }
+  return key_from_lcs(lcs_tri[tri_index(i, j, k)], lens[i], lens[j]);
+}
+
+static void write_lambda(const okey *lam, int32_t k, uint64_t *lnum, uint32_t *lden) {
+  for (int32_t j = 0; j < k; ++j) key_reduce(lam[j], &lnum[j], &lden[j]);
+}
+
+/*
+ * (i) Sibson's SLINK.  Point n is inserted with M(j) = d(j, n) for j < n:
+ *   pi(n) = n, lambda(n) = inf;
+ *   for j = 0..n-1: if lambda(j) >= M(j): M(pi(j)) = min(M(pi(j)), lambda(j));
+ *                   lambda(j) = M(j); pi(j) = n;
+ *                 else M(pi(j)) = min(M(pi(j)), M(j));
+ *   for j = 0..n-1: if lambda(j) >= lambda(pi(j)): pi(j) = n.
+ * Distances come from a row callback so the k x k matrix need not exist.
+ */
+typedef void (*row_fn)(void *ctx, int32_t n, okey *M);
+
+static int slink_core(int32_t k, row_fn fn, void *ctx, int32_t *pi, uint64_t *lnum,
+                      uint32_t *lden) {
+  okey *lam = (okey *)malloc(sizeof(okey) * (size_t)k);
+  okey *M = (okey *)malloc(sizeof(okey) * (size_t)k);
+  if (!lam || !M) { free(lam); free(M); return -2; }
+  pi[0] = 0;
+  lam[0] = KEY_INF;
+  for (int32_t n = 1; n < k; ++n) {
+    pi[n] = n;
+    lam[n] = KEY_INF;
+    fn(ctx, n, M);
+    for (int32_t j = 0; j < n; ++j) {
+      int32_t p = pi[j];
+      if (!key_lt(lam[j], M[j])) {
+        M[p] = key_min(M[p], lam[j]);
+        lam[j] = M[j];
+        pi[j] = n;
+      } else {
+        M[p] = key_min(M[p], M[j]);
+      }
+    }
+    for (int32_t j = 0; j < n; ++j)
+      if (!key_lt(lam[j], lam[pi[j]])) pi[j] = n;
+  }
+  write_lambda(lam, k, lnum, lden);
+  free(lam);
+  free(M);
+  return 0;
+}
+
+typedef struct { const int32_t *lcs_tri; const int32_t *lens; int32_t k; } tri_ctx;
+static void tri_row(void *c, int32_t n, okey *M) {
+  tri_ctx *t = (tri_ctx *)c;
+  for (int32_t j = 0; j < n; ++j) M[j] = tri_key(t->lcs_tri, t->lens, t->k, j, n);
+}
+
+int oracle_slink_matrix(const int32_t *lcs_tri, const int32_t *lens, int32_t k, int32_t *pi,
+                        uint64_t *lnum, uint32_t *lden) {
+  if (k < 1) return -1;
+  tri_ctx c = {lcs_tri, lens, k};
+  return slink_core(k, tri_row, &c, pi, lnum, lden);
+}
+
+/* streamed: row n's LCS values are computed by DP when point n is inserted */
+typedef struct {
+  const uint8_t *res; const int64_t *off; int32_t k; int32_t *lcs; int32_t **rows; int nrows;
+} dp_ctx;
+static void dp_row(void *c, int32_t n, okey *M) {
+  dp_ctx *t = (dp_ctx *)c;
+  const uint8_t *a = t->res + t->off[n];
+  int32_t la = (int32_t)(t->off[n + 1] - t->off[n]);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int32_t j = 0; j < n; ++j) {
+#ifdef _OPENMP
+    int32_t *row = t->rows[omp_get_thread_num()];
+#else
+    int32_t *row = t->rows[0];
+#endif
+    int32_t lb = (int32_t)(t->off[j + 1] - t->off[j]);
+    int32_t L = lcs_dp(t->res + t->off[j], lb, a, la, row);
+    M[j] = key_from_lcs(L, lb, la);
+  }
+}
+
+int oracle_slink_streamed(const uint8_t *res, const int64_t *off, int32_t k, int32_t *pi,
+                          uint64_t *lnum, uint32_t *lden, int nthreads) {
+  if (k < 1) return -1;
+  set_threads(nthreads);
+  int nt = oracle_num_threads();
+  int32_t ml = max_len(off, k);
+  int32_t **rows = (int32_t **)calloc((size_t)nt, sizeof(int32_t *));
+  if (!rows) return -2;
+  int rc = 0;
+  for (int t = 0; t < nt; ++t) {
+    rows[t] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ml + 1));
+    if (!rows[t]) rc = -2;
+  }
+  if (rc == 0) {
+    dp_ctx c = {res, off, k, NULL, rows, nt};
+    rc = slink_core(k, dp_row, &c, pi, lnum, lden);
+  }
+  for (int t = 0; t < nt; ++t) free(rows[t]);
+  free(rows);
+  return rc;
+}
+
+/*
+ * (ii) Naive O(k^3) agglomeration.  Active clusters carry their largest
+ * index; the closest pair (ties: lowest (a, b) cluster indices) is merged at
+ * height h with single-link distances min(d(A,C), d(B,C)).  Merging clusters
+ * with largest indices a < b sets lambda(a) = h, pi(a) = b.  A final pass in
+ * descending j replaces pi(j) by pi(pi(j)) while lambda(pi(j)) == lambda(j),
+ * so that pi(j) is the largest index of j's cluster at height lambda(j).
+ */
+int oracle_slink_naive(const int32_t *lcs_tri, const int32_t *lens, int32_t k, int32_t *pi,
+                       uint64_t *lnum, uint32_t *lden) {
+  if (k < 1) return -1;
+  okey *D = (okey *)malloc(sizeof(okey) * (size_t)k * (size_t)k);
+  okey *lam = (okey *)malloc(sizeof(okey) * (size_t)k);
+  int32_t *maxid = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  char *alive = (char *)malloc((size_t)k);
+  if (!D || !lam || !maxid || !alive) { free(D); free(lam); free(maxid); free(alive); return -2; }
+  for (int32_t a = 0; a < k; ++a) {
+    alive[a] = 1; maxid[a] = a; lam[a] = KEY_INF; pi[a] = a;
+    for (int32_t b = 0; b < k; ++b)
+      D[(size_t)a * k + b] = a == b ? KEY_INF : tri_key(lcs_tri, lens, k, a, b);
+  }
+  for (int32_t step = 0; step + 1 < k; ++step) {
+    int32_t ba = -1, bb = -1;
+    okey best = KEY_INF;
+    for (int32_t a = 0; a < k; ++a) {
+      if (!alive[a]) continue;
+      for (int32_t b = a + 1; b < k; ++b) {
+        if (!alive[b]) continue;
+        okey d = D[(size_t)a * k + b];
+        if (ba < 0 || key_lt(d, best)) { best = d; ba = a; bb = b; }
+      }
+    }
+    /* clusters ba and bb merge at height best; keep slot ba */
+    int32_t ma = maxid[ba], mb = maxid[bb];
+    int32_t lo = ma < mb ? ma : mb, hi = ma < mb ? mb : ma;
+    lam[lo] = best;
+    pi[lo] = hi;
+    maxid[ba] = hi;
+    alive[bb] = 0;
+    for (int32_t c = 0; c < k; ++c) {
+      if (!alive[c] || c == ba) continue;
+      okey m = key_min(D[(size_t)ba * k + c], D[(size_t)bb * k + c]);
+      D[(size_t)ba * k + c] = m;
+      D[(size_t)c * k + ba] = m;
+    }
+  }
+  for (int32_t j = k - 2; j >= 0; --j) {
+    while (pi[j] != k - 1 && pi[pi[j]] != pi[j] && !key_lt(lam[j], lam[pi[j]]) &&
+           !key_lt(lam[pi[j]], lam[j]))
+      pi[j] = pi[pi[j]];
+  }
+  write_lambda(lam, k, lnum, lden);
+  free(D); free(lam); free(maxid); free(alive);
+  return 0;
+}
+
+/*
+ * (iii) The definition.  u = minimax closure of the complete graph:
+ * u(i,j) = min over m of max(u(i,m), u(m,j)) (Floyd-Warshall order), then
+ * lambda(j) = min_{l>j} u(j,l), pi(j) = max{ l > j : u(j,l) <= lambda(j) };
+ * the last point is the root with pi = itself and lambda = +inf.
+ */
+int oracle_slink_definition(const int32_t *lcs_tri, const int32_t *lens, int32_t k, int32_t *pi,
+                            uint64_t *lnum, uint32_t *lden) {
+  if (k < 1) return -1;
+  okey *U = (okey *)malloc(sizeof(okey) * (size_t)k * (size_t)k);
+  okey *lam = (okey *)malloc(sizeof(okey) * (size_t)k);
+  if (!U || !lam) { free(U); free(lam); return -2; }
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < k; ++b)
+      U[(size_t)a * k + b] = a == b ? (okey){0, 1} : tri_key(lcs_tri, lens, k, a, b);
+  for (int32_t m = 0; m < k; ++m)
+    for (int32_t a = 0; a < k; ++a)
+      for (int32_t b = 0; b < k; ++b) {
+        okey via = key_max(U[(size_t)a * k + m], U[(size_t)m * k + b]);
+        if (key_lt(via, U[(size_t)a * k + b])) U[(size_t)a * k + b] = via;
+      }
+  for (int32_t j = 0; j < k; ++j) {
+    okey best = KEY_INF;
+    for (int32_t l = j + 1; l < k; ++l) best = key_min(best, U[(size_t)j * k + l]);
+    lam[j] = best;
+    int32_t p = j;
+    for (int32_t l = j + 1; l < k; ++l)
+      if (!key_lt(best, U[(size_t)j * k + l])) p = l;
+    if (j == k - 1) { p = j; lam[j] = KEY_INF; }
+    pi[j] = p;
+  }
+  write_lambda(lam, k, lnum, lden);
+  free(U); free(lam);
+  return 0;
+}
+
+/* minimax closure exposed for ultrametric tests: u as reduced (num, den) */
+int oracle_minimax(const int32_t *lcs_tri, const int32_t *lens, int32_t k, uint64_t *unum,
+                   uint32_t *uden) {
+  if (k < 1) return -1;
+  okey *U = (okey *)malloc(sizeof(okey) * (size_t)k * (size_t)k);
+  if (!U) return -2;
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < k; ++b)
+      U[(size_t)a * k + b] = a == b ? (okey){0, 1} : tri_key(lcs_tri, lens, k, a, b);
+  for (int32_t m = 0; m < k; ++m)
+    for (int32_t a = 0; a < k; ++a)
+      for (int32_t b = 0; b < k; ++b) {
+        okey via = key_max(U[(size_t)a * k + m], U[(size_t)m * k + b]);
+        if (key_lt(via, U[(size_t)a * k + b])) U[(size_t)a * k + b] = via;
+      }
+  for (size_t t = 0; t < (size_t)k * k; ++t) key_reduce(U[t], &unum[t], &uden[t]);
+  free(U);
+  return 0;
+}
+
+/* ------------------------------------------------------------ merges */
+static int32_t uf_find(int32_t *parent, int32_t x) {
+  while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+  return x;
+}
+
+/* insertion-free ordering: merge sort of indices by (lambda, j) */
+static const uint64_t *g_num;
+static const uint32_t *g_den;
+static int order_lt(int32_t a, int32_t b) {
+  okey ka = {g_num[a], g_den[a]}, kb = {g_num[b], g_den[b]};
+  if (key_lt(ka, kb)) return 1;
+  if (key_lt(kb, ka)) return 0;
+  return a < b;
+}
+static void msort(int32_t *v, int32_t *tmp, int32_t n) {
+  if (n < 2) return;
+  int32_t h = n / 2;
+  msort(v, tmp, h);
+  msort(v + h, tmp, n - h);
+  int32_t i = 0, j = h, t = 0;
+  while (i < h && j < n) tmp[t++] = order_lt(v[j], v[i]) ? v[j++] : v[i++];
+  while (i < h) tmp[t++] = v[i++];
+  while (j < n) tmp[t++] = v[j++];
+  memcpy(v, tmp, sizeof(int32_t) * (size_t)n);
+}
+
+/*
+ * Merge list from the pointer representation: j in [0, k-1) sorted by
+ * (lambda(j), j) ascending; for each, the clusters of j and pi(j) merge at
+ * height lambda(j).  Output per merge t: (smaller id, larger id), the height
+ * as a reduced fraction and the new cluster's size; the new cluster gets
+ * id k + t.  lnum/lden are reduced fractions (as written by the tree
+ * functions above).
+ */
+int oracle_merges(const int32_t *pi, const uint64_t *lnum, const uint32_t *lden, int32_t k,
+                  int32_t *merges, uint64_t *hnum, uint32_t *hden, int32_t *sizes) {
+  if (k < 1) return -1;
+  if (k == 1) return 0;
+  int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t *cid = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t *csize = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  if (!ord || !tmp || !parent || !cid || !csize) {
+    free(ord); free(tmp); free(parent); free(cid); free(csize);
+    return -2;
+  }
+  for (int32_t j = 0; j < k; ++j) { ord[j] = j; parent[j] = j; cid[j] = j; csize[j] = 1; }
+  g_num = lnum; g_den = lden;
+  msort(ord, tmp, k - 1);
+  for (int32_t t = 0; t < k - 1; ++t) {
+    int32_t j = ord[t];
+    int32_t a = uf_find(parent, j), b = uf_find(parent, pi[j]);
+    int32_t ia = cid[a], ib = cid[b];
+    merges[2 * t] = ia < ib ? ia : ib;
+    merges[2 * t + 1] = ia < ib ? ib : ia;
+    hnum[t] = lnum[j];
+    hden[t] = lden[j];
+    parent[a] = b;
+    csize[b] += csize[a];
+    cid[b] = k + t;
+    sizes[t] = csize[b];
+  }
+  free(ord); free(tmp); free(parent); free(cid); free(csize);
+  return 0;
+}
