@@ -156,10 +156,16 @@ void famsa_free(famsa_family *f);
 
 /*
  * famsa_last_stats -- counters of the last famsa_slink_tree call on this
- * handle (for benchmarks): kernel launches, LCS cell updates and word
- * steps, and re-layouts that needed a run merge.  stats[8] int64:
- *   0 launches, 1 cells, 2 word_steps, 3 pairs, 4 relayout_merges,
- *   5 merge_rounds, 6 rows, 7 reserved.
+ * handle (for benchmarks).  stats[16] int64:
+ *   0 kernel launches of the tree build, 1 LCS cells (sum of |A||B| over
+ *   pairs), 2 LCS word steps (64-bit words of the Peq side times symbols of
+ *   the other side, summed over pairs), 3 pairs, 4 insertions whose re-layout
+ *   needed a run merge, 5 run-merge rounds, 6 points, 7 device time of the
+ *   LCS kernels in ns (CUDA events around each row block), 8 device time of
+ *   the row-update kernels in ns, 9 device time of the finalisation in ns,
+ *   10 LCS kernel launches, 11 kernel launches of famsa_pack_peq for this
+ *   handle, 12..15 reserved.
+ * Returns EINVAL for NULL arguments.
  */
 int famsa_last_stats(const famsa_family *f, int64_t *stats);
 

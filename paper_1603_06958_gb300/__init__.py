@@ -155,9 +155,10 @@ class Family:
             pass
 
     def stats(self) -> dict:
-        s = np.zeros(8, dtype=np.int64)
+        s = np.zeros(16, dtype=np.int64)
         _check(load().famsa_last_stats(self.handle, s.ctypes.data), "famsa_last_stats")
-        keys = ["launches", "cells", "word_steps", "pairs", "relayout_merges", "merge_rounds", "rows"]
+        keys = ["launches", "cells", "word_steps", "pairs", "relayout_merges", "merge_rounds", "rows",
+                "lcs_ns", "update_ns", "finalize_ns", "lcs_launches", "pack_launches"]
         return {k: int(v) for k, v in zip(keys, s)}
 
 

@@ -69,7 +69,8 @@ struct Family {
 
   // scratch reused across calls
   std::vector<DeviceBuffer> scratch;
-  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t stats[16] = {0};
+  int64_t pack_launches = 0;
 };
 
 // Allocation with an injectable failure hook (tests use it to check ENOMEM paths).

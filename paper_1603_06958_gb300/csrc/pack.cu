@@ -331,6 +331,13 @@ int pack_family(const uint8_t *residues, const int64_t *offsets, int32_t k, bool
   CK(cudaStreamSynchronize(st));
   dev_free(keys); dev_free(keys2); dev_free(words); dev_free(gbytes); dev_free(d_tot);
   dev_free(d_status);
+  {
+    int64_t passes = 0;
+    for (int64_t width = 1; width < k; width *= 2) ++passes;
+    // k_lengths, k_codes, k_sort_keys, merge passes, k_sorted_fields, 2 scans,
+    // k_group_sizes, k_pack_peq, k_col_layout
+    f->pack_launches = 9 + passes;
+  }
   *out = f;
   return FAMSA_OK;
 

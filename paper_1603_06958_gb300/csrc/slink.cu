@@ -694,7 +694,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
                int32_t *merges_out, uint64_t *hnum_out, uint32_t *hden_out, int32_t *sizes_out,
                bool out_on_device, cudaStream_t st) {
   const int32_t k = f->k;
-  for (int i = 0; i < 8; ++i) f->stats[i] = 0;
+  for (int i = 0; i < 16; ++i) f->stats[i] = 0;
   cudaError_t err = cudaSuccess;
   int cl = 0;
   if (g_force_cluster) cl = g_force_cluster;
@@ -708,8 +708,17 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
               upd_done[2] = {nullptr, nullptr};
   Scratch sc;
   sc.st = st;
-  int64_t launches = 0;
+  int64_t launches = 0, lcs_launches = 0;
   int rc = FAMSA_OK;
+  // timing events: per row block, LCS begin/end on sA and update begin/end on sB
+  std::vector<cudaEvent_t> tev;
+  auto timing_event = [&](cudaStream_t s) -> cudaError_t {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    tev.push_back(e);
+    return cudaEventRecord(e, s);
+  };
 
 #define CKE(x)                                       \
   do {                                               \
@@ -820,7 +829,9 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       b.ld = ld;
       b.row0 = r0;
       b.triangle = true;
-      CKE(launch_lcs(b, sA, &launches));
+      CKE(timing_event(sA));
+      CKE(launch_lcs(b, sA, &lcs_launches));
+      CKE(timing_event(sA));
       CKE(cudaEventRecord(lcs_done[buf], sA));
       CKE(cudaStreamWaitEvent(sB, lcs_done[buf], 0));
       SlinkArgs args;
@@ -840,11 +851,14 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       attr.val.clusterDim.z = 1;
       cfg.attrs = &attr;
       cfg.numAttrs = 1;
+      CKE(timing_event(sB));
       CKE(cudaLaunchKernelEx(&cfg, k_slink_rows, args));
       ++launches;
+      CKE(timing_event(sB));
       CKE(cudaEventRecord(upd_done[buf], sB));
     }
     // finalise on sB
+    CKE(timing_event(sB));
     const int T = 256;
     unsigned nb = (unsigned)((k + T - 1) / T);
     if (k >= 2) {
@@ -878,6 +892,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       CKE(cudaStreamSynchronize(sB));
     }
     CKE(cudaGetLastError());
+    CKE(timing_event(sB));
     // outputs
     cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (pi_out) CKE(cudaMemcpyAsync(pi_out, cpi, sizeof(int32_t) * k, kind, sB));
@@ -894,6 +909,26 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     CKE(cudaEventRecord(ev_end, sB));
     CKE(cudaStreamWaitEvent(st, ev_end, 0));
     CKE(cudaEventSynchronize(ev_end));
+    {
+      // events: 4 per row block (LCS begin/end, update begin/end), then 2 for finalisation
+      double lcs_ms = 0, upd_ms = 0, fin_ms = 0;
+      const size_t nblk = (tev.size() - 2) / 4;
+      for (size_t i = 0; i < nblk; ++i) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, tev[4 * i], tev[4 * i + 1]);
+        cudaEventElapsedTime(&b, tev[4 * i + 2], tev[4 * i + 3]);
+        lcs_ms += a;
+        upd_ms += b;
+      }
+      float c = 0;
+      cudaEventElapsedTime(&c, tev[tev.size() - 2], tev[tev.size() - 1]);
+      fin_ms = c;
+      f->stats[7] = (int64_t)(lcs_ms * 1e6);
+      f->stats[8] = (int64_t)(upd_ms * 1e6);
+      f->stats[9] = (int64_t)(fin_ms * 1e6);
+      f->stats[10] = lcs_launches;
+    }
+    launches += lcs_launches;
     f->stats[0] = launches;
     f->stats[1] = cells;
     f->stats[2] = words;
@@ -917,6 +952,7 @@ done:
     if (lcs_done[i]) cudaEventDestroy(lcs_done[i]);
     if (upd_done[i]) cudaEventDestroy(upd_done[i]);
   }
+  for (cudaEvent_t e : tev) cudaEventDestroy(e);
   return rc;
 #undef CKE
 }
