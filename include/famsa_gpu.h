@@ -156,7 +156,7 @@ void famsa_free(famsa_family *f);
 
 /*
  * famsa_last_stats -- counters of the last famsa_slink_tree call on this
- * handle (for benchmarks).  stats[16] int64:
+ * handle (for benchmarks).  stats[24] int64:
  *   0 kernel launches of the tree build, 1 LCS cells (sum of |A||B| over
  *   pairs), 2 LCS word steps (64-bit words of the Peq side times symbols of
  *   the other side, summed over pairs), 3 pairs, 4 insertions whose re-layout
@@ -164,7 +164,11 @@ void famsa_free(famsa_family *f);
  *   LCS kernels in ns (CUDA events around each row block), 8 device time of
  *   the row-update kernels in ns, 9 device time of the finalisation in ns,
  *   10 LCS kernel launches, 11 kernel launches of famsa_pack_peq for this
- *   handle, 12..15 reserved.
+ *   handle, 12 row-update kernel (1 cluster shared memory, 2 global memory),
+ *   13 its cluster size, 14..17 kilocycles spent by one thread of the
+ *   shared-memory kernel in its four phases (distances and scan summaries;
+ *   scans and pointer update; shift re-layout; run-merge re-layout),
+ *   18..23 reserved.
  * Returns EINVAL for NULL arguments.
  */
 int famsa_last_stats(const famsa_family *f, int64_t *stats);

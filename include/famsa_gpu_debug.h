@@ -25,6 +25,21 @@ int famsa_debug_set_tpp_max_w(int w);
  * Results are identical for every size.  Returns FAMSA_EINVAL otherwise. */
 int famsa_debug_set_cluster(int ctas);
 
+/* Select the row-update kernel: 0 automatic (cluster shared memory when the
+ * family fits, else global memory), 1 cluster shared memory (the tree call
+ * returns FAMSA_EINVAL when the family does not fit), 2 global memory.
+ * Results are identical.  Returns FAMSA_EINVAL outside 0..2. */
+int famsa_debug_set_update_path(int path);
+
+/* The pointer representation produced by the row updates of the last
+ * famsa_slink_tree call on f, in insertion labels: points are inserted in
+ * the family's (length, index) order; perm[j] is the caller's label of the
+ * j-th inserted point, pi[j] / (lam_num[j], lam_den[j]) its pointer and
+ * height (reduced; +inf = (1, 0)).  Host arrays of k entries; any may be
+ * NULL.  Returns FAMSA_EINVAL when no tree was built on f. */
+int famsa_debug_insertion_state(const famsa_family *f, int32_t *perm, int32_t *pi,
+                                uint64_t *lam_num, uint32_t *lam_den);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
             "famsa_debug_fail_alloc_after": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_tpp_max_w": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_cluster": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_insertion_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -155,10 +157,12 @@ class Family:
             pass
 
     def stats(self) -> dict:
-        s = np.zeros(16, dtype=np.int64)
+        s = np.zeros(24, dtype=np.int64)
         _check(load().famsa_last_stats(self.handle, s.ctypes.data), "famsa_last_stats")
         keys = ["launches", "cells", "word_steps", "pairs", "relayout_merges", "merge_rounds", "rows",
-                "lcs_ns", "update_ns", "finalize_ns", "lcs_launches", "pack_launches"]
+                "lcs_ns", "update_ns", "finalize_ns", "lcs_launches", "pack_launches",
+                "update_path", "update_cluster", "phaseA_kcycles", "phaseB_kcycles",
+                "phaseC_kcycles", "phaseD_kcycles"]
         return {k: int(v) for k, v in zip(keys, s)}
 
 
@@ -264,6 +268,22 @@ def debug_fail_alloc_after(n: int):
 def debug_set_tpp_max_w(w: int):
     """Rows wider than w words use the warp-per-pair kernel (32 = default)."""
     _check(load().famsa_debug_set_tpp_max_w(w), "famsa_debug_set_tpp_max_w")
+
+
+def debug_set_update_path(path: int):
+    """0 automatic, 1 cluster shared-memory row update, 2 global-memory row update."""
+    _check(load().famsa_debug_set_update_path(path), "famsa_debug_set_update_path")
+
+
+def debug_insertion_state(fam: Family) -> dict:
+    """Pointer representation of the last tree build, in insertion labels."""
+    k = fam.k
+    out = {"perm": np.empty(k, np.int32), "pi": np.empty(k, np.int32),
+           "lambda_num": np.empty(k, np.uint64), "lambda_den": np.empty(k, np.uint32)}
+    _check(load().famsa_debug_insertion_state(fam.handle, *[out[n].ctypes.data for n in
+                                                            ("perm", "pi", "lambda_num", "lambda_den")]),
+           "famsa_debug_insertion_state")
+    return out
 
 
 def debug_set_cluster(ctas: int):

@@ -100,7 +100,7 @@ void famsa_free(famsa_family *fh) {
 int famsa_last_stats(const famsa_family *fh, int64_t *stats) {
   if (!fh || !stats) return FAMSA_EINVAL;
   const Family *f = reinterpret_cast<const Family *>(fh);
-  for (int i = 0; i < 16; ++i) stats[i] = f->stats[i];
+  for (int i = 0; i < kStatsLen; ++i) stats[i] = f->stats[i];
   stats[11] = f->pack_launches;
   return FAMSA_OK;
 }

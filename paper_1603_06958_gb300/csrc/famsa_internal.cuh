@@ -20,6 +20,7 @@ constexpr int kMaxLen = 65535;
 constexpr int kGroup = 32;          // columns per group (one warp)
 constexpr int kChunk = 16;          // residues per interleaved chunk (one 16-byte load)
 constexpr int kTppMaxW = 32;        // thread-per-pair handles rows of up to 32 words
+constexpr int kStatsLen = 24;       // famsa_last_stats entries
 
 // Peq layout (row side): for each sequence s and word w, 64 uint32:
 //   [0..32)  low 32 bits of the mask for symbols 0..31
@@ -69,8 +70,11 @@ struct Family {
 
   // scratch reused across calls
   std::vector<DeviceBuffer> scratch;
-  int64_t stats[16] = {0};
+  int64_t stats[kStatsLen] = {0};
   int64_t pack_launches = 0;
+  // insertion-label pointer representation of the last tree build (debug export):
+  // per point j: original label, pi, packed lambda key, 0
+  std::vector<int64_t> dbg_state;
 };
 
 // Allocation with an injectable failure hook (tests use it to check ENOMEM paths).

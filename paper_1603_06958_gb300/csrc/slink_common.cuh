@@ -1,0 +1,217 @@
+// Shared device helpers of the single-linkage row update: exact distance keys,
+// clamp-function scans, the row-update state and small sorts.
+//
+// FAMSA Methods, "Determination of the guide tree": single linkage by SLINK
+// (Sibson 1973), computed from the similarity rows one new point at a time.
+// Pairs are ordered by the exact rational distance indel^2 / LCS (the
+// paper's similarity LCS / indel^2 reversed; "Pairwise similarities
+// calculation"), indel = |A| + |B| - 2 LCS.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "famsa_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace famsa {
+
+// ----------------------------------------------------------------- keys
+// Packed exact distance: (indel^2 << 16) | LCS, indel^2 < 2^34, LCS <= 65535.
+// LCS = 0 gives +inf, encoded (1 << 16) (num 1, den 0); 0 has num 0.
+// a < b by cross multiplication (products < 2^50, no overflow).
+constexpr uint64_t kKeyInf = 1ull << 16;
+constexpr uint64_t kKeyZero = 1ull;
+
+__host__ __device__ __forceinline__ bool klt(uint64_t a, uint64_t b) {
+  return (a >> 16) * (b & 0xffffu) < (b >> 16) * (a & 0xffffu);
+}
+__host__ __device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) { return klt(b, a) ? b : a; }
+__host__ __device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) { return klt(a, b) ? b : a; }
+__device__ __forceinline__ uint64_t make_key(uint32_t L, uint32_t la, uint32_t lb) {
+  if (L == 0) return kKeyInf;
+  uint64_t indel = (uint64_t)(la + lb - 2 * L);
+  return ((indel * indel) << 16) | L;
+}
+
+// ----------------------------------------------------------------- clamps
+// The minimax distance from a new point n along a dendrogram leaf order
+// (u(x_p, x_q) = max gap between p and q) satisfies
+//   Lf[q] = min(d[q], max(Lf[q-1], gap[q-1])),  Rf[q] = min(d[q], max(Rf[q+1], gap[q])),
+//   D[q]  = min(Lf[q], Rf[q]).
+// Each step is the clamp x -> min(hi, max(x, lo)); clamps compose into
+// clamps, so the recurrences run as parallel scans.
+struct Clamp {
+  uint64_t lo, hi;
+};
+__device__ __forceinline__ Clamp identity_clamp() { return Clamp{kKeyZero, kKeyInf}; }
+// a, then b
+__device__ __forceinline__ Clamp compose(const Clamp &a, const Clamp &b) {
+  return Clamp{kmax(a.lo, b.lo), kmin(b.hi, kmax(a.hi, b.lo))};
+}
+__device__ __forceinline__ Clamp shfl_clamp_up(const Clamp &c, int d) {
+  return Clamp{__shfl_up_sync(0xffffffffu, c.lo, d), __shfl_up_sync(0xffffffffu, c.hi, d)};
+}
+__device__ __forceinline__ Clamp shfl_clamp_down(const Clamp &c, int d) {
+  return Clamp{__shfl_down_sync(0xffffffffu, c.lo, d), __shfl_down_sync(0xffffffffu, c.hi, d)};
+}
+
+// Block-level exclusive scans of clamps, forward (thread order) and backward
+// (reverse thread order) at once.  sw needs 4*32+2 entries.  Returns the
+// thread's exclusive prefixes and the block totals.
+__device__ __forceinline__ void block_scan2(Clamp vf, Clamp vb, Clamp *pf, Clamp *pb, Clamp *tf,
+                                            Clamp *tb, Clamp *sw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  Clamp incf = vf, incb = vb;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    Clamp yf = shfl_clamp_up(incf, d);
+    Clamp yb = shfl_clamp_down(incb, d);
+    if (lane >= d) incf = compose(yf, incf);
+    if (lane + d < 32) incb = compose(yb, incb);
+  }
+  Clamp excf = shfl_clamp_up(incf, 1);
+  Clamp excb = shfl_clamp_down(incb, 1);
+  if (lane == 0) excf = identity_clamp();
+  if (lane == 31) excb = identity_clamp();
+  if (lane == 31) sw[warp] = incf;
+  if (lane == 0) sw[32 + warp] = incb;
+  __syncthreads();
+  if (warp == 0) {
+    Clamp wf = lane < nw ? sw[lane] : identity_clamp();
+    Clamp wb = lane < nw ? sw[32 + lane] : identity_clamp();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Clamp yf = shfl_clamp_up(wf, d);
+      Clamp yb = shfl_clamp_down(wb, d);
+      if (lane >= d) wf = compose(yf, wf);
+      if (lane + d < 32) wb = compose(yb, wb);
+    }
+    Clamp ef = shfl_clamp_up(wf, 1);
+    Clamp eb = shfl_clamp_down(wb, 1);
+    if (lane == 0) ef = identity_clamp();
+    if (lane >= nw - 1) eb = identity_clamp();
+    if (lane < nw) { sw[64 + lane] = ef; sw[96 + lane] = eb; }
+    if (lane == nw - 1) sw[128] = wf;
+    if (lane == 0) sw[129] = wb;
+  }
+  __syncthreads();
+  *pf = compose(sw[64 + warp], excf);
+  *pb = compose(sw[96 + warp], excb);
+  *tf = sw[128];
+  *tb = sw[129];
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------- state
+// Row-update state, one entry per position of the current dendrogram leaf
+// order.  Buffers alternate with the number of points: the layout of m
+// points is in buffer m & 1.  lam/pi are Sibson's pointer representation of
+// the point at that position (insertion labels); they move with the point.
+struct SlinkState {
+  int32_t *ord[2];   // point (insertion label)
+  int32_t *olen[2];  // its length
+  uint64_t *gap[2];  // gap[p] = minimax distance between positions p and p+1
+  uint64_t *lam[2];
+  int32_t *pi[2];
+  uint64_t *D;       // minimax distances to the new point (global kernel)
+  // run-merge buffers (positions), ping-pong
+  uint64_t *mD[2];
+  int32_t *mOrd[2], *mLen[2], *mOld[2], *mPi[2];
+  uint64_t *mLam[2];
+  uint64_t *mGap;    // old gaps (cluster shared-memory kernel's merge path)
+  int32_t *runsA, *runsB;  // run starts, unsorted
+  uint64_t *ctl;
+  const int32_t *slen;     // lengths in insertion order
+};
+
+constexpr int kSlinkThreads = 1024;
+constexpr int kMaxClusterCtas = 16;
+constexpr int kRunsSmem = 2048;  // natural-run merges keep up to this many run starts per side
+
+// ctl layout (uint64 words)
+constexpr int kCtlAggL = 0;                               // 2 words per CTA
+constexpr int kCtlAggR = kCtlAggL + 2 * kMaxClusterCtas;
+constexpr int kCtlArg = kCtlAggR + 2 * kMaxClusterCtas;   // 2 words per CTA
+constexpr int kCtlCnt = kCtlArg + 2 * kMaxClusterCtas;    // 6 words: run counts A,B, 3 slots
+constexpr int kCtlStats = kCtlCnt + 6;                    // merges, rounds, phase cycles A..D
+constexpr int kCtlWords = kCtlStats + 8;
+
+__device__ __forceinline__ void chunk_of(int32_t m, int32_t tid, int32_t nthreads, int32_t *b,
+                                         int32_t *e) {
+  int32_t c = (m + nthreads - 1) / nthreads;
+  int64_t bb = (int64_t)tid * c;
+  *b = (int32_t)(bb < m ? bb : (int64_t)m);
+  *e = (int32_t)(bb + c < m ? bb + c : (int64_t)m);
+}
+
+// index of the last run start <= i (starts sorted ascending, starts[0] <= i)
+__device__ __forceinline__ int32_t run_of(const int32_t *starts, int32_t nruns, int32_t i) {
+  int32_t lo = 0, hi = nruns - 1;
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// in-place bitonic sort of n ints in shared memory (cap: power of two >= n)
+__device__ __forceinline__ void smem_sort(int32_t *a, int32_t n, int32_t cap) {
+  for (int32_t i = n + threadIdx.x; i < cap; i += blockDim.x) a[i] = INT32_MAX;
+  __syncthreads();
+  for (int32_t size = 2; size <= cap; size <<= 1) {
+    for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+        int32_t j = i ^ stride;
+        if (j > i) {
+          bool up = (i & size) == 0;
+          int32_t x = a[i], y = a[j];
+          if ((x > y) == up) { a[i] = y; a[j] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Stable pairwise merge of sorted runs on one side of the re-layout.  The
+// left side (positions < x0) sorts by D descending, the right side ascending;
+// an element of the left run of a pair counts partner elements strictly
+// before it, an element of the right run counts partner elements before or
+// equal.  Returns the number of partner elements that precede value v.
+__device__ __forceinline__ int32_t merge_count(const uint64_t *key, int32_t sbase, int32_t ps,
+                                               int32_t pe, uint64_t v, bool left_side,
+                                               bool in_left_run) {
+  int32_t lo = ps, hi = pe;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    uint64_t w = key[sbase + mid];
+    bool before;
+    if (left_side) before = in_left_run ? klt(v, w) : !klt(w, v);
+    else before = in_left_run ? klt(w, v) : !klt(v, w);
+    if (before) lo = mid + 1; else hi = mid;
+  }
+  return lo - ps;
+}
+
+// Buffers for the finalisation (all device, caller-owned)
+struct FinBufs {
+  int32_t *idx, *posof, *it, *rt, *pi, *sub_lo, *sub_hi, *ordA, *ordB, *rank, *sorder, *merges,
+      *sizes;
+  uint64_t *gt, *lam, *hkey, *lnum, *hnum;
+  uint32_t *lden, *hden;
+  int64_t *sz, *szpre, *tot;
+};
+
+size_t fin_levels(int32_t k);
+cudaError_t launch_finalize(const int32_t *ord, const uint64_t *gap, const int32_t *perm, int32_t k,
+                            FinBufs &B, cudaStream_t st, int64_t *launches);
+cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
+                                int32_t r1, int cl, cudaStream_t st);
+int max_cluster_global();
+size_t smem_bytes_for(int32_t P);
+int smem_cluster_for(int32_t k, int force);
+cudaError_t launch_slink_smem(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
+                              int32_t r1, int cl, int32_t k, cudaStream_t st);
+
+}  // namespace famsa

@@ -27,6 +27,7 @@ def fg():
     m.load()
     yield m
     m.debug_set_cluster(0)
+    m.debug_set_update_path(0)
 
 
 def oracle_tree(res, off):
@@ -96,21 +97,55 @@ def test_degenerate_families(fg):
     assert (got["lambda_den"] == 0).all()
 
 
-@pytest.mark.parametrize("ctas", [1, 2, 4, 8])
-def test_cluster_sizes_agree(fg, ctas):
+@pytest.mark.parametrize("path,ctas", [(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (2, 8)])
+def test_update_paths_and_cluster_sizes_agree(fg, path, ctas):
+    # path 1: state in cluster shared memory, path 2: state in global memory
     res, off = synth.family(400, 11, root_len=150, alphabet=4, dup_frac=0.05)
+    fg.debug_set_update_path(path)
     fg.debug_set_cluster(ctas)
     try:
-        got, _ = run_tree(fg, res, off)
+        got, st = run_tree(fg, res, off)
     finally:
         fg.debug_set_cluster(0)
+        fg.debug_set_update_path(0)
+    assert st["update_path"] == path and st["update_cluster"] == ctas
     assert_same_tree(got, oracle_tree(res, off))
 
 
-def test_relayout_merges_exercised(fg):
+@pytest.mark.parametrize("path", [1, 2])
+def test_row_update_pointer_state_matches_sibson(fg, path):
+    # The row updates keep Sibson's pointer representation of the points in
+    # insertion order ((length, index) order); the oracle's SLINK run over the
+    # family permuted into that order must give the same pi / lambda.
+    res, off = synth.family(500, 21, root_len=90, alphabet=3, dup_frac=0.05)
+    fg.debug_set_update_path(path)
+    try:
+        fam = fg.pack_peq(res, off)
+        fg.slink_tree(fam)
+        stt = fg.debug_insertion_state(fam)
+        fam.free()
+    finally:
+        fg.debug_set_update_path(0)
+    perm = stt["perm"]
+    lens = np.diff(off)
+    assert np.array_equal(perm, np.lexsort((np.arange(len(lens)), lens)))
+    seqs = [res[off[i]:off[i + 1]] for i in perm]
+    pres = np.concatenate(seqs)
+    poff = np.concatenate([[0], np.cumsum([len(x) for x in seqs])]).astype(np.int64)
+    pi, ln, ld = oracle.slink_matrix(oracle.lcs_allpairs(pres, poff), np.diff(poff).astype(np.int32))
+    assert np.array_equal(stt["pi"], pi)
+    assert np.array_equal(stt["lambda_num"], ln) and np.array_equal(stt["lambda_den"], ld)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_relayout_merges_exercised(fg, path):
     # a tie-heavy family whose insertions need run merges in the re-layout
     res, off = synth.family(600, 12, root_len=40, alphabet=3, sub_rate=0.1)
-    got, st = run_tree(fg, res, off)
+    fg.debug_set_update_path(path)
+    try:
+        got, st = run_tree(fg, res, off)
+    finally:
+        fg.debug_set_update_path(0)
     assert_same_tree(got, oracle_tree(res, off))
     assert st["relayout_merges"] > 0 and st["merge_rounds"] >= st["relayout_merges"]
 
@@ -158,4 +193,3 @@ def test_plain20k_full_tree_against_oracle_digest(fg):
     k = len(off) - 1
     pi = got["pi"]
     assert (pi[:-1] > np.arange(k - 1)).all() and pi[-1] == k - 1
-    assert np.all(np.diff(got["sizes"]) != 0) or True
