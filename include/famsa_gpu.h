@@ -166,9 +166,11 @@ void famsa_free(famsa_family *f);
  *   10 LCS kernel launches, 11 kernel launches of famsa_pack_peq for this
  *   handle, 12 row-update kernel (1 cluster shared memory, 2 global memory),
  *   13 its cluster size, 14..17 kilocycles spent by one thread of the
- *   shared-memory kernel in its four phases (distances and scan summaries;
- *   scans and pointer update; shift re-layout; run-merge re-layout),
- *   18..23 reserved.
+ *   shared-memory kernel in its phases (14 unused; 15 scans, pointer update
+ *   and prefetch; 16 shift re-layout plus the next point's distances;
+ *   17 run-merge re-layout), 18 1 when keys used the 32-bit-numerator
+ *   packing, 19 run merges done in shared memory, 20 the runs they
+ *   merged (both sides), 21..23 reserved.
  * Returns EINVAL for NULL arguments.
  */
 int famsa_last_stats(const famsa_family *f, int64_t *stats);

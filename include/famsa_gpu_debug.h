@@ -40,6 +40,19 @@ int famsa_debug_set_update_path(int path);
 int famsa_debug_insertion_state(const famsa_family *f, int32_t *perm, int32_t *pi,
                                 uint64_t *lam_num, uint32_t *lam_den);
 
+/* Threads per CTA of the shared-memory row-update kernel (128, 256 or 512;
+ * 0 = default 512).  Results are identical.  Returns FAMSA_EINVAL otherwise. */
+int famsa_debug_set_update_threads(int threads);
+
+/* 1: the LCS of a row block waits for the row update of the previous block
+ * (no overlap of the two streams), for timing studies; 0: overlap (default). */
+int famsa_debug_set_serial(int on);
+
+/* Kilocycles spent by one thread of the shared-memory row-update kernel in
+ * the sub-steps of its last tree build on f (out16: 16 int64; 0..7 the
+ * common path, 8..13 the run merge in shared memory). */
+int famsa_debug_sub_kcycles(const famsa_family *f, int64_t *out16);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,9 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_tpp_max_w": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_cluster": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_serial": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
             "famsa_debug_insertion_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -162,7 +165,8 @@ class Family:
         keys = ["launches", "cells", "word_steps", "pairs", "relayout_merges", "merge_rounds", "rows",
                 "lcs_ns", "update_ns", "finalize_ns", "lcs_launches", "pack_launches",
                 "update_path", "update_cluster", "phaseA_kcycles", "phaseB_kcycles",
-                "phaseC_kcycles", "phaseD_kcycles"]
+                "phaseC_kcycles", "phaseD_kcycles", "narrow_keys",
+                "fast_merges", "fast_merge_runs"]
         return {k: int(v) for k, v in zip(keys, s)}
 
 
@@ -284,6 +288,21 @@ def debug_insertion_state(fam: Family) -> dict:
                                                             ("perm", "pi", "lambda_num", "lambda_den")]),
            "famsa_debug_insertion_state")
     return out
+
+
+def debug_set_update_threads(threads: int):
+    """Threads per CTA of the shared-memory row update (0 = default)."""
+    _check(load().famsa_debug_set_update_threads(threads), "famsa_debug_set_update_threads")
+
+
+def debug_set_serial(on: bool):
+    load().famsa_debug_set_serial(int(on))
+
+
+def debug_sub_kcycles(fam: Family):
+    out = np.zeros(16, np.int64)
+    _check(load().famsa_debug_sub_kcycles(fam.handle, out.ctypes.data), "famsa_debug_sub_kcycles")
+    return out.tolist()
 
 
 def debug_set_cluster(ctas: int):

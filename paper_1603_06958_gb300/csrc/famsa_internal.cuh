@@ -72,6 +72,7 @@ struct Family {
   std::vector<DeviceBuffer> scratch;
   int64_t stats[kStatsLen] = {0};
   int64_t pack_launches = 0;
+  int64_t sub_kcycles[16] = {0};
   // insertion-label pointer representation of the last tree build (debug export):
   // per point j: original label, pi, packed lambda key, 0
   std::vector<int64_t> dbg_state;

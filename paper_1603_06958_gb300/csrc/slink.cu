@@ -21,6 +21,7 @@ namespace famsa {
 
 static int g_force_cluster = 0;
 static int g_update_path = 0;  // 0 automatic, 1 shared-memory kernel, 2 global-memory kernel
+static int g_serial = 0;       // 1: no overlap of LCS and row update (timing studies)
 
 struct Scratch {
   std::vector<void *> ptrs;
@@ -57,6 +58,9 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     path = cl ? 1 : 2;
   }
   if (path == 2) cl = g_force_cluster ? g_force_cluster : max_cluster_global();
+  // the shared-memory kernel packs keys as (num << 32) | den when every
+  // indel^2 fits in 32 bits (all lengths <= 32767)
+  const bool narrow = path == 1 && f->max_len <= 32767;
 
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
@@ -105,6 +109,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       S.mOld[i] = sc.get<int32_t>(kp);
       S.mLam[i] = sc.get<uint64_t>(kp);
       S.mPi[i] = sc.get<int32_t>(kp);
+      S.mRaw[i] = sc.get<int32_t>(kp);
     }
     S.D = sc.get<uint64_t>(kp);
     S.mGap = sc.get<uint64_t>(kp);
@@ -115,7 +120,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     // row blocks: about 128 MB of 16-bit LCS values per buffer
     int32_t B = (int32_t)std::min<int64_t>(std::max<int64_t>((int64_t)(1 << 26) / std::max(k, 1), 64), 2048);
     B = std::min(B, std::max(k - 1, 1));
-    const int64_t ld = k;
+    const int64_t ld = (k + 1) & ~1;  // even: rows start on 4-byte boundaries
     uint16_t *rowbuf[2];
     rowbuf[0] = sc.get<uint16_t>((size_t)B * ld);
     rowbuf[1] = sc.get<uint16_t>((size_t)B * ld);
@@ -142,7 +147,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     {
       // the layout of one point (point 0): buffer 1
       std::vector<int32_t> z1 = {0};
-      std::vector<uint64_t> inf1 = {kKeyInf};
+      std::vector<uint64_t> inf1 = {narrow ? KeysNarrow::kInf : KeysWide::kInf};
       CKE(cudaMemcpyAsync(S.ord[1], z1.data(), sizeof(int32_t), cudaMemcpyHostToDevice, st));
       CKE(cudaMemcpyAsync(S.olen[1], f->d_slen, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
       CKE(cudaMemcpyAsync(S.lam[1], inf1.data(), sizeof(uint64_t), cudaMemcpyHostToDevice, st));
@@ -167,6 +172,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       const int32_t r1 = std::min(r0 + B, k);
       const int buf = blk & 1;
       if (blk >= 2) CKE(cudaStreamWaitEvent(sA, upd_done[buf], 0));
+      if (g_serial && blk >= 1) CKE(cudaStreamWaitEvent(sA, upd_done[buf ^ 1], 0));
       LcsBatch b;
       b.peq = f->d_peq;
       b.colres = f->d_colres;
@@ -194,14 +200,18 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       CKE(cudaEventRecord(lcs_done[buf], sA));
       CKE(cudaStreamWaitEvent(sB, lcs_done[buf], 0));
       CKE(timing_event(sB));
-      if (path == 1) CKE(launch_slink_smem(S, rowbuf[buf], ld, r0, r1, cl, k, sB));
+      if (path == 1) CKE(launch_slink_smem(S, rowbuf[buf], ld, r0, r1, cl, k, narrow, sB));
       else CKE(launch_slink_global(S, rowbuf[buf], ld, r0, r1, cl, sB));
       ++launches;
       CKE(timing_event(sB));
       CKE(cudaEventRecord(upd_done[buf], sB));
     }
-    // finalisation from the layout of k points (buffer k & 1)
+    // finalisation from the layout of k points (buffer k & 1), keys in the wide packing
     CKE(timing_event(sB));
+    if (narrow) {
+      CKE(widen_keys(S.gap[k & 1], k - 1, sB));
+      CKE(widen_keys(S.lam[k & 1], k, sB));
+    }
     if (k >= 2) {
       CKE(launch_finalize(S.ord[k & 1], S.gap[k & 1], f->d_perm, k, FB, sB, &launches));
     } else {
@@ -235,8 +245,12 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       CKE(cudaMemcpyAsync(ordh.data(), S.ord[bk], sizeof(int32_t) * k, cudaMemcpyDeviceToHost, sB));
       CKE(cudaMemcpyAsync(pih.data(), S.pi[bk], sizeof(int32_t) * k, cudaMemcpyDeviceToHost, sB));
       CKE(cudaMemcpyAsync(lamh.data(), S.lam[bk], sizeof(uint64_t) * k, cudaMemcpyDeviceToHost, sB));
-      uint64_t hstats[6] = {0, 0, 0, 0, 0, 0};
-      CKE(cudaMemcpyAsync(hstats, S.ctl + kCtlStats, sizeof(uint64_t) * 6, cudaMemcpyDeviceToHost, sB));
+      uint64_t hstats[24] = {0};
+      CKE(cudaMemcpyAsync(hstats, S.ctl + kCtlStats, sizeof(uint64_t) * 24, cudaMemcpyDeviceToHost, sB));
+      f->stats[18] = narrow ? 1 : 0;
+      for (int i = 0; i < 16; ++i) f->sub_kcycles[i] = (int64_t)(hstats[8 + i] / 1000);
+      f->stats[19] = (int64_t)hstats[6];
+      f->stats[20] = (int64_t)hstats[7];
       CKE(cudaEventRecord(ev_end, sB));
       CKE(cudaStreamWaitEvent(st, ev_end, 0));
       CKE(cudaEventSynchronize(ev_end));
@@ -304,6 +318,18 @@ done:
 extern "C" int famsa_debug_set_cluster(int ctas) {
   if (ctas != 0 && ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8 && ctas != 16) return FAMSA_EINVAL;
   famsa::g_force_cluster = ctas;
+  return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_set_serial(int on) {
+  famsa::g_serial = on ? 1 : 0;
+  return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_sub_kcycles(const famsa_family *fh, int64_t *out16) {
+  if (!fh || !out16) return FAMSA_EINVAL;
+  const famsa::Family *f = reinterpret_cast<const famsa::Family *>(fh);
+  for (int i = 0; i < 16; ++i) out16[i] = f->sub_kcycles[i];
   return FAMSA_OK;
 }
 

@@ -34,6 +34,34 @@ __device__ __forceinline__ uint64_t make_key(uint32_t L, uint32_t la, uint32_t l
   return ((indel * indel) << 16) | L;
 }
 
+// Two packings of the same exact key.  Wide: (num << 16) | den, any length
+// up to 65535.  Narrow: (num << 32) | den, when every length is <= 32767 so
+// that num = indel^2 < 2^32; a comparison is then two 32x32->64 multiplies.
+struct KeysWide {
+  static constexpr uint64_t kInf = 1ull << 16;
+  static constexpr uint64_t kZero = 1ull;
+  __device__ __forceinline__ static bool lt(uint64_t a, uint64_t b) { return klt(a, b); }
+  __device__ __forceinline__ static uint64_t make(uint32_t L, uint32_t la, uint32_t lb) {
+    return make_key(L, la, lb);
+  }
+  __device__ __forceinline__ static uint64_t wide(uint64_t k) { return k; }
+};
+struct KeysNarrow {
+  static constexpr uint64_t kInf = 1ull << 32;
+  static constexpr uint64_t kZero = 1ull;
+  __device__ __forceinline__ static bool lt(uint64_t a, uint64_t b) {
+    return (uint64_t)(uint32_t)(a >> 32) * (uint32_t)b < (uint64_t)(uint32_t)(b >> 32) * (uint32_t)a;
+  }
+  __device__ __forceinline__ static uint64_t make(uint32_t L, uint32_t la, uint32_t lb) {
+    if (L == 0) return kInf;
+    const uint32_t indel = la + lb - 2 * L;
+    return ((uint64_t)(indel * indel) << 32) | L;
+  }
+  __device__ __forceinline__ static uint64_t wide(uint64_t k) {
+    return ((k >> 32) << 16) | (k & 0xffffffffull);
+  }
+};
+
 // ----------------------------------------------------------------- clamps
 // The minimax distance from a new point n along a dendrogram leaf order
 // (u(x_p, x_q) = max gap between p and q) satisfies
@@ -44,10 +72,16 @@ __device__ __forceinline__ uint64_t make_key(uint32_t L, uint32_t la, uint32_t l
 struct Clamp {
   uint64_t lo, hi;
 };
-__device__ __forceinline__ Clamp identity_clamp() { return Clamp{kKeyZero, kKeyInf}; }
+template <class K>
+__device__ __forceinline__ uint64_t kmin_t(uint64_t a, uint64_t b) { return K::lt(b, a) ? b : a; }
+template <class K>
+__device__ __forceinline__ uint64_t kmax_t(uint64_t a, uint64_t b) { return K::lt(a, b) ? b : a; }
+template <class K = KeysWide>
+__device__ __forceinline__ Clamp identity_clamp() { return Clamp{K::kZero, K::kInf}; }
 // a, then b
+template <class K = KeysWide>
 __device__ __forceinline__ Clamp compose(const Clamp &a, const Clamp &b) {
-  return Clamp{kmax(a.lo, b.lo), kmin(b.hi, kmax(a.hi, b.lo))};
+  return Clamp{kmax_t<K>(a.lo, b.lo), kmin_t<K>(b.hi, kmax_t<K>(a.hi, b.lo))};
 }
 __device__ __forceinline__ Clamp shfl_clamp_up(const Clamp &c, int d) {
   return Clamp{__shfl_up_sync(0xffffffffu, c.lo, d), __shfl_up_sync(0xffffffffu, c.hi, d)};
@@ -59,6 +93,7 @@ __device__ __forceinline__ Clamp shfl_clamp_down(const Clamp &c, int d) {
 // Block-level exclusive scans of clamps, forward (thread order) and backward
 // (reverse thread order) at once.  sw needs 4*32+2 entries.  Returns the
 // thread's exclusive prefixes and the block totals.
+template <class K = KeysWide>
 __device__ __forceinline__ void block_scan2(Clamp vf, Clamp vb, Clamp *pf, Clamp *pb, Clamp *tf,
                                             Clamp *tb, Clamp *sw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -67,37 +102,37 @@ __device__ __forceinline__ void block_scan2(Clamp vf, Clamp vb, Clamp *pf, Clamp
   for (int d = 1; d < 32; d <<= 1) {
     Clamp yf = shfl_clamp_up(incf, d);
     Clamp yb = shfl_clamp_down(incb, d);
-    if (lane >= d) incf = compose(yf, incf);
-    if (lane + d < 32) incb = compose(yb, incb);
+    if (lane >= d) incf = compose<K>(yf, incf);
+    if (lane + d < 32) incb = compose<K>(yb, incb);
   }
   Clamp excf = shfl_clamp_up(incf, 1);
   Clamp excb = shfl_clamp_down(incb, 1);
-  if (lane == 0) excf = identity_clamp();
-  if (lane == 31) excb = identity_clamp();
+  if (lane == 0) excf = identity_clamp<K>();
+  if (lane == 31) excb = identity_clamp<K>();
   if (lane == 31) sw[warp] = incf;
   if (lane == 0) sw[32 + warp] = incb;
   __syncthreads();
   if (warp == 0) {
-    Clamp wf = lane < nw ? sw[lane] : identity_clamp();
-    Clamp wb = lane < nw ? sw[32 + lane] : identity_clamp();
+    Clamp wf = lane < nw ? sw[lane] : identity_clamp<K>();
+    Clamp wb = lane < nw ? sw[32 + lane] : identity_clamp<K>();
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       Clamp yf = shfl_clamp_up(wf, d);
       Clamp yb = shfl_clamp_down(wb, d);
-      if (lane >= d) wf = compose(yf, wf);
-      if (lane + d < 32) wb = compose(yb, wb);
+      if (lane >= d) wf = compose<K>(yf, wf);
+      if (lane + d < 32) wb = compose<K>(yb, wb);
     }
     Clamp ef = shfl_clamp_up(wf, 1);
     Clamp eb = shfl_clamp_down(wb, 1);
-    if (lane == 0) ef = identity_clamp();
-    if (lane >= nw - 1) eb = identity_clamp();
+    if (lane == 0) ef = identity_clamp<K>();
+    if (lane >= nw - 1) eb = identity_clamp<K>();
     if (lane < nw) { sw[64 + lane] = ef; sw[96 + lane] = eb; }
     if (lane == nw - 1) sw[128] = wf;
     if (lane == 0) sw[129] = wb;
   }
   __syncthreads();
-  *pf = compose(sw[64 + warp], excf);
-  *pb = compose(sw[96 + warp], excb);
+  *pf = compose<K>(sw[64 + warp], excf);
+  *pb = compose<K>(sw[96 + warp], excb);
   *tf = sw[128];
   *tb = sw[129];
   __syncthreads();
@@ -117,7 +152,7 @@ struct SlinkState {
   uint64_t *D;       // minimax distances to the new point (global kernel)
   // run-merge buffers (positions), ping-pong
   uint64_t *mD[2];
-  int32_t *mOrd[2], *mLen[2], *mOld[2], *mPi[2];
+  int32_t *mOrd[2], *mLen[2], *mOld[2], *mPi[2], *mRaw[2];
   uint64_t *mLam[2];
   uint64_t *mGap;    // old gaps (cluster shared-memory kernel's merge path)
   int32_t *runsA, *runsB;  // run starts, unsorted
@@ -134,8 +169,8 @@ constexpr int kCtlAggL = 0;                               // 2 words per CTA
 constexpr int kCtlAggR = kCtlAggL + 2 * kMaxClusterCtas;
 constexpr int kCtlArg = kCtlAggR + 2 * kMaxClusterCtas;   // 2 words per CTA
 constexpr int kCtlCnt = kCtlArg + 2 * kMaxClusterCtas;    // 6 words: run counts A,B, 3 slots
-constexpr int kCtlStats = kCtlCnt + 6;                    // merges, rounds, phase cycles A..D
-constexpr int kCtlWords = kCtlStats + 8;
+constexpr int kCtlStats = kCtlCnt + 6;                    // merges, rounds, phase cycles A..D, fast merges, sub-phase cycles
+constexpr int kCtlWords = kCtlStats + 24;
 
 __device__ __forceinline__ void chunk_of(int32_t m, int32_t tid, int32_t nthreads, int32_t *b,
                                          int32_t *e) {
@@ -179,6 +214,7 @@ __device__ __forceinline__ void smem_sort(int32_t *a, int32_t n, int32_t cap) {
 // an element of the left run of a pair counts partner elements strictly
 // before it, an element of the right run counts partner elements before or
 // equal.  Returns the number of partner elements that precede value v.
+template <class K = KeysWide>
 __device__ __forceinline__ int32_t merge_count(const uint64_t *key, int32_t sbase, int32_t ps,
                                                int32_t pe, uint64_t v, bool left_side,
                                                bool in_left_run) {
@@ -187,8 +223,8 @@ __device__ __forceinline__ int32_t merge_count(const uint64_t *key, int32_t sbas
     int32_t mid = (lo + hi) >> 1;
     uint64_t w = key[sbase + mid];
     bool before;
-    if (left_side) before = in_left_run ? klt(v, w) : !klt(w, v);
-    else before = in_left_run ? klt(w, v) : !klt(v, w);
+    if (left_side) before = in_left_run ? K::lt(v, w) : !K::lt(w, v);
+    else before = in_left_run ? K::lt(w, v) : !K::lt(v, w);
     if (before) lo = mid + 1; else hi = mid;
   }
   return lo - ps;
@@ -212,6 +248,7 @@ int max_cluster_global();
 size_t smem_bytes_for(int32_t P);
 int smem_cluster_for(int32_t k, int force);
 cudaError_t launch_slink_smem(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
-                              int32_t r1, int cl, int32_t k, cudaStream_t st);
+                              int32_t r1, int cl, int32_t k, bool narrow, cudaStream_t st);
+cudaError_t widen_keys(uint64_t *key, int32_t n, cudaStream_t st);
 
 }  // namespace famsa

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kSlinkThreads, 1) k_slink_global(GlobalArgs a)
         S.mOld[0][p] = p;
         S.mLam[0][p] = lam[p];
         S.mPi[0][p] = pi[p];
+        S.mRaw[0][p] = 0;
       }
       if (tid == 0) ctl[kCtlStats] += 1;
       cluster.sync();

@@ -15,6 +15,7 @@ namespace famsa {
 // sides are in sRunsA[0..nA) / sRunsB[0..nB) (sorted) when natural, else
 // every element starts as its own run.  Threads own positions [cb, ce).
 // Returns the buffer index holding the merged order.
+template <class K = KeysWide>
 __device__ __forceinline__ int merge_rounds(SlinkState &S, cg::cluster_group &cluster, int32_t m,
                                             int32_t x0, bool natural, const int32_t *sRunsA,
                                             int32_t nA, const int32_t *sRunsB, int32_t nB,
@@ -56,7 +57,7 @@ __device__ __forceinline__ int merge_rounds(SlinkState &S, cg::cluster_group &cl
       const uint64_t v = S.mD[src][p];
       int32_t np = p;
       if (pairs) {
-        const int32_t cnt = merge_count(S.mD[src], sbase, ps, pe, v, left, (run & 1) == 0);
+        const int32_t cnt = merge_count<K>(S.mD[src], sbase, ps, pe, v, left, (run & 1) == 0);
         np = sbase + min(rs, ps) + (i - rs) + cnt;
       }
       S.mD[dst][np] = v;
@@ -65,6 +66,7 @@ __device__ __forceinline__ int merge_rounds(SlinkState &S, cg::cluster_group &cl
       S.mOld[dst][np] = S.mOld[src][p];
       S.mLam[dst][np] = S.mLam[src][p];
       S.mPi[dst][np] = S.mPi[src][p];
+      S.mRaw[dst][np] = S.mRaw[src][p];
     }
     cluster.sync();
     src = dst;

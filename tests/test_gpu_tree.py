@@ -28,6 +28,7 @@ def fg():
     yield m
     m.debug_set_cluster(0)
     m.debug_set_update_path(0)
+    m.debug_set_update_threads(0)
 
 
 def oracle_tree(res, off):
@@ -112,6 +113,18 @@ def test_update_paths_and_cluster_sizes_agree(fg, path, ctas):
     assert_same_tree(got, oracle_tree(res, off))
 
 
+@pytest.mark.parametrize("threads", [128, 256])
+def test_update_thread_counts_agree(fg, threads):
+    res, off = synth.family(700, 41, root_len=60, alphabet=3, sub_rate=0.1)
+    fg.debug_set_update_threads(threads)
+    try:
+        got, st = run_tree(fg, res, off)
+    finally:
+        fg.debug_set_update_threads(0)
+    assert st["relayout_merges"] > 0
+    assert_same_tree(got, oracle_tree(res, off))
+
+
 @pytest.mark.parametrize("path", [1, 2])
 def test_row_update_pointer_state_matches_sibson(fg, path):
     # The row updates keep Sibson's pointer representation of the points in
@@ -147,7 +160,39 @@ def test_relayout_merges_exercised(fg, path):
     finally:
         fg.debug_set_update_path(0)
     assert_same_tree(got, oracle_tree(res, off))
-    assert st["relayout_merges"] > 0 and st["merge_rounds"] >= st["relayout_merges"]
+    assert st["relayout_merges"] > 0
+    if path == 2:  # the global-memory kernel merges pairwise, one round or more per merge
+        assert st["merge_rounds"] >= st["relayout_merges"]
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_long_sequence_wide_keys(fg, path):
+    # a sequence longer than 32767 forces the 16-bit-denominator key packing
+    rng = np.random.default_rng(31)
+    base = rng.integers(0, 20, 200).astype(np.uint8)
+    seqs = []
+    for i in range(40):
+        s = base.copy()
+        s[rng.random(200) < 0.2] = rng.integers(0, 20, int((rng.random(200) < 0.2).sum()) or 1)[0]
+        seqs.append(s)
+    seqs.append(np.tile(base, 170)[:33000])
+    seqs.append(rng.integers(0, 20, 40000).astype(np.uint8))
+    res = np.concatenate(seqs)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in seqs])]).astype(np.int64)
+    fg.debug_set_update_path(path)
+    try:
+        got, st = run_tree(fg, res, off)
+    finally:
+        fg.debug_set_update_path(0)
+    assert st["narrow_keys"] == 0
+    assert_same_tree(got, oracle_tree(res, off))
+
+
+def test_narrow_keys_used_for_short_families(fg):
+    res, off = synth.family(300, 32, root_len=100)
+    got, st = run_tree(fg, res, off)
+    assert st["update_path"] == 1 and st["narrow_keys"] == 1
+    assert_same_tree(got, oracle_tree(res, off))
 
 
 def test_plain1k_tree(fg):
