@@ -47,7 +47,8 @@ typedef enum {
   FAMSA_ENOMEM = 3,   /* device or host allocation failed */
   FAMSA_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed */
   FAMSA_ETIMEOUT = 5, /* a bounded device-side wait gave up */
-  FAMSA_EBUSY = 6     /* the serving queue is full */
+  FAMSA_EBUSY = 6,    /* the serving queue is full */
+  FAMSA_ELIMIT = 7    /* beyond the fixed limits of famsa_lcs_query_noalloc */
 } famsa_status;
 
 /* Opaque handle: a packed family resident on the device.  It owns a device
@@ -149,6 +150,48 @@ int famsa_slink_tree(const famsa_family *f, int32_t *pi, uint64_t *lambda_num,
 int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_offsets,
                     int32_t nq, int q_on_device, int32_t *out, int out_on_device,
                     void *cuda_stream);
+
+/*
+ * famsa_lcs_query_noalloc -- famsa_lcs_query for callers that cannot
+ * allocate device memory at call time.  The paper has no counterpart: it is
+ * an interface of this library only.
+ *
+ * Some callers hand all their device memory out up front (a serving process
+ * that reserves its whole budget in its own arena, or shares the GPU with a
+ * framework that owns the rest of it), so a call that allocates fails or
+ * takes memory they cannot spare; on a latency-bound request path an
+ * allocation can also wait for the device.  This entry point allocates
+ * nothing: its scratch (the queries' match-bitmask tables and row list) is
+ * a fixed array of FAMSA_NOALLOC_SCRATCH_BYTES in the library's device
+ * memory, one per device.
+ *
+ * q, q_offsets: nq query sequences in the family format, ON THE DEVICE.
+ * nq: 1..FAMSA_NOALLOC_MAX_QUERIES.
+ * max_len: an upper bound on every query's length, 1..FAMSA_NOALLOC_MAX_LEN
+ *   (each query is computed with ceil(max_len / 64) words, so a tight bound
+ *   is faster).
+ * out: nq*k int32 ON THE DEVICE, out[i*k + j] = LCS(query i, member j), the
+ *   same values famsa_lcs_query gives.
+ * Errors: EINVAL (NULL argument, nq or max_len < 1, a query length outside
+ *   1..max_len, a residue code >= 25: the last two found on the device, in
+ *   which case out is undefined), ELIMIT (nq or max_len beyond the limits
+ *   above; nothing is enqueued), ECUDA.
+ * The call returns after its stream has finished (it reads the validation
+ * status back).
+ * Set-up: the first call on a device looks the array's address up on that
+ * device (cudaGetSymbolAddress), so make that first call before any stream
+ * capture on the device.
+ * Sharing: every call on a device uses the same array, which keeps what the
+ * last call wrote there; each call rewrites all of it that it reads.  Calls
+ * whose GPU work overlaps (on different streams, from different threads or
+ * on different handles) race on the array: serialise them, for example on
+ * one stream.
+ */
+#define FAMSA_NOALLOC_MAX_QUERIES 64
+#define FAMSA_NOALLOC_MAX_LEN 4096
+#define FAMSA_NOALLOC_SCRATCH_BYTES (1048576 + 4096)
+int famsa_lcs_query_noalloc(const famsa_family *f, const uint8_t *q, const int64_t *q_offsets,
+                            int32_t nq, int32_t max_len, int32_t *out, void *cuda_stream);
 
 /* Release a handle and its device memory (NULL is ignored).  Waits for the
  * handle's pending work. */

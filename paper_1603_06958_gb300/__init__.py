@@ -26,7 +26,9 @@ LIB_PATH = os.path.join(_HERE, "libfamsa_gpu.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 HEADERS = [os.path.join(INCLUDE, h) for h in ("famsa_gpu.h", "famsa_gpu_debug.h")]
 
-FAMSA_OK, FAMSA_EINVAL, FAMSA_ERANGE, FAMSA_ENOMEM, FAMSA_ECUDA, FAMSA_ETIMEOUT, FAMSA_EBUSY = range(7)
+FAMSA_OK, FAMSA_EINVAL, FAMSA_ERANGE, FAMSA_ENOMEM, FAMSA_ECUDA, FAMSA_ETIMEOUT, FAMSA_EBUSY, \
+    FAMSA_ELIMIT = range(8)
+NOALLOC_MAX_QUERIES, NOALLOC_MAX_LEN = 64, 4096
 
 _lib = None
 _lock = threading.Lock()
@@ -69,6 +71,7 @@ def load(path: str = LIB_PATH):
             "famsa_lcs_rows": ([_P, i32, i32, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_slink_tree": ([_P, _P, u64p, _P, _P, u64p, _P, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_lcs_query": ([_P, _P, _P, i32, ctypes.c_int, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_lcs_query_noalloc": ([_P, _P, _P, i32, i32, _P, _P], ctypes.c_int),
             "famsa_free": ([_P], None),
             "famsa_last_stats": ([_P, _P], ctypes.c_int),
             "famsa_debug_fail_alloc_after": ([ctypes.c_int], ctypes.c_int),
@@ -258,6 +261,29 @@ def famsa_lcs_query(fam: Family, q_residues, q_offsets, out=None, device: bool =
 
 
 lcs_query = famsa_lcs_query
+
+
+def famsa_lcs_query_noalloc(fam: Family, q_residues, q_offsets, max_len: int, out=None,
+                            stream=None):
+    """famsa_lcs_query with no device allocation inside the call: device inputs
+    and output only, at most NOALLOC_MAX_QUERIES queries of at most
+    NOALLOC_MAX_LEN residues (max_len bounds them all); (nq, k) int32."""
+    nq = len(q_offsets) - 1
+    qp, qdev = _ptr(q_residues)
+    op, odev = _ptr(q_offsets)
+    if not (qdev and odev):
+        raise ValueError("famsa_lcs_query_noalloc takes device inputs")
+    if out is None:
+        out = _empty(nq * fam.k, np.int32, True)
+    p, dev = _ptr(out)
+    if not dev:
+        raise ValueError("famsa_lcs_query_noalloc writes a device output")
+    _check(load().famsa_lcs_query_noalloc(fam.handle, qp, op, nq, int(max_len), p,
+                                          _stream_ptr(stream)), "famsa_lcs_query_noalloc")
+    return out.reshape(nq, fam.k)
+
+
+lcs_query_noalloc = famsa_lcs_query_noalloc
 
 
 def famsa_free(fam: Family):
