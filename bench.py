@@ -12,7 +12,12 @@ canonical pointer representation + merge list (famsa_slink_tree).
 Metric: cell updates per second of the whole step in GCUPS, where cells =
 sum over pairs of |A||B| (pairs/s is reported beside it).  The roofline of
 the dominant kernel (thread-per-pair LCS) is integer-ALU bound: 6 INT32 ops
-per 64-cell word step against 152 SMs x 128 INT32 lanes x 2.07 GHz.
+per 64-cell word step (LOP3 and 32-bit adds with carry, which issue on the
+ALU pipe only) against 152 SMs x 64 ALU-pipe lanes x 2.07 GHz; the figure
+for all 128 INT32 lanes (ALU + FMA pipes) is reported beside it.
+
+python bench.py --int-peaks measures the integer pipe widths the roofline
+uses (independent LOP3 / IADD3 / IMAD chains over the whole device).
 
 N > 1 (torchrun) runs independent replicas, one family per GPU (the path
 does not shard); value is the total cells of all ranks / the slowest rank.
@@ -33,7 +38,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "all-pairs LCS GCUPS + pairs/s on 1 GB300 vs plain; INT32 roofline fraction"
-SMS, INT32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+SMS, SM_MAX_GHZ = 152, 2.07
+ALU_LANES = 64      # LOP3 / IADD3 lanes per SM per clock (ALU pipe; --int-peaks)
+INT32_LANES = 128   # ALU + FMA pipes together
 OPS_PER_WORD_STEP = 6
 WORKLOADS = {
     "plain20k": "plain large family: k=20,000, root length log-normal (median 300, sigma 0.4), "
@@ -146,18 +153,17 @@ def cpu_baseline(res, off, budget_s=15.0):
     k = len(off) - 1
     lens = np.diff(off).astype(np.int64)
     prefix = np.concatenate([[0], np.cumsum(lens)])
-    # calibrate on the last 2 rows, then take as many trailing rows as fit the budget
-    t0 = time.perf_counter()
-    oracle.lcs_rows(res, off, k - 2, k)
-    t_cal = time.perf_counter() - t0
-    cal_cells = float(sum(lens[i] * prefix[i] for i in range(k - 2, k)))
-    rate = cal_cells / max(t_cal, 1e-6)
-    per_row = float(lens[-1] * prefix[k - 1])
-    rows = int(max(2, min(k - 1, budget_s * rate / max(per_row, 1))))
-    r0 = k - rows
-    t0 = time.perf_counter()
-    oracle.lcs_rows(res, off, r0, k)
-    dt = time.perf_counter() - t0
+    # grow the trailing-row sample until one run takes at least half the budget
+    # (small samples under-use the host threads, so their rate is not extrapolated)
+    rows = 4
+    while True:
+        r0 = k - rows
+        t0 = time.perf_counter()
+        oracle.lcs_rows(res, off, r0, k)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * budget_s or rows >= k - 1:
+            break
+        rows = int(min(k - 1, rows * max(2.0, 0.75 * budget_s / max(dt, 1e-3))))
     cells = float(sum(lens[i] * prefix[i] for i in range(r0, k)))
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": oracle.num_threads(),
             "kind": "oracle",
@@ -293,7 +299,8 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return 0
     achieved = OPS_PER_WORD_STEP * word_steps / (lcs_ms * 1e-3) / 1e12
-    peak = SMS * INT32_LANES * SM_MAX_GHZ * 1e9 / 1e12
+    peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9 / 1e12
+    peak_all = SMS * INT32_LANES * SM_MAX_GHZ * 1e9 / 1e12
     tr = recorded_traffic()
     line = {
         "metric": METRIC,
@@ -319,8 +326,12 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak,
                      "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                      "kernel": "k_lcs_tpp (thread-per-pair bit-parallel LCS)",
-                     "peak_note": "derived: 152 SMs x 128 INT32 lanes x 2.07 GHz max SM clock "
+                     "peak_note": "derived: 152 SMs x 64 ALU-pipe lanes x 2.07 GHz max SM "
+                                  "clock; LOP3 and IADD3 issue on the ALU pipe only, 64 lanes "
+                                  "per SM per clock as measured by bench.py --int-peaks "
                                   "(MEASURED_PEAKS.json has no integer peak)",
+                     "peak_all_int32_lanes": peak_all,
+                     "frac_all_int32_lanes": achieved / peak_all,
                      "achieved_note": "6 INT32 ops per 64-cell word step x word steps / summed "
                                       "CUDA-event time of the LCS launches of the step"},
         "e2e": {"value": cells_total / (e2e_max * 1e-3) / 1e9, "unit": "GCUPS",
@@ -331,6 +342,29 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res, off, args.cpu_budget)
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_int_peaks():
+    """Instruction rates of independent LOP3 / IADD3 / IMAD chains, as lanes per SM per clock."""
+    import torch
+    import paper_1603_06958_gb300 as fg
+    fg.load()
+    torch.cuda.init()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {"sms": sms, "kinds": {}}
+    for kind, name in enumerate(["lop3", "iadd3", "imad", "lop3+imad"]):
+        fg.debug_int_pipe_rate(kind)  # warm-up
+        clk = ClockSampler(0)
+        clk.start()
+        rates = [fg.debug_int_pipe_rate(kind) for _ in range(20)]
+        c = clk.stop()
+        rate = float(np.median(rates))
+        mhz = c.get("sm_mhz") or SM_MAX_GHZ * 1e3
+        out["kinds"][name] = {"inst_per_s": rate, "sm_mhz": mhz,
+                              "lanes_per_sm_per_clk": rate / (sms * mhz * 1e6),
+                              "clock_reasons": c.get("reasons")}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -346,12 +380,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=int, default=12)
+    ap.add_argument("--int-peaks", action="store_true",
+                    help="measure the integer pipe widths used by the roofline, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.int_peaks:
+        return run_int_peaks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:

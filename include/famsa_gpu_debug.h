@@ -6,6 +6,8 @@
 #ifndef FAMSA_GPU_DEBUG_H
 #define FAMSA_GPU_DEBUG_H
 
+#include "famsa_gpu.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -52,6 +54,12 @@ int famsa_debug_set_serial(int on);
  * the sub-steps of its last tree build on f (out16: 16 int64; 0..7 the
  * common path, 8..13 the run merge in shared memory). */
 int famsa_debug_sub_kcycles(const famsa_family *f, int64_t *out16);
+
+/* Thread-instructions per second of one integer instruction kind run as
+ * many independent chains over the whole device (kind 0 LOP3, 1 IADD3,
+ * 2 IMAD, 3 LOP3 and IMAD alternating); it measures the width of the ALU
+ * and FMA pipes for the LCS roofline.  Allocates a small output buffer. */
+int famsa_debug_int_pipe_rate(int kind, double *inst_per_s);
 
 #ifdef __cplusplus
 }

@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_serial": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
+            "famsa_debug_int_pipe_rate": ([ctypes.c_int, _P], ctypes.c_int),
             "famsa_debug_insertion_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -329,6 +330,14 @@ def debug_sub_kcycles(fam: Family):
     out = np.zeros(16, np.int64)
     _check(load().famsa_debug_sub_kcycles(fam.handle, out.ctypes.data), "famsa_debug_sub_kcycles")
     return out.tolist()
+
+
+def debug_int_pipe_rate(kind: int) -> float:
+    """Thread-instructions/s of independent LOP3 (0), IADD3 (1), IMAD (2) or
+    LOP3+IMAD (3) chains over the whole device."""
+    out = ctypes.c_double()
+    _check(load().famsa_debug_int_pipe_rate(kind, ctypes.byref(out)), "famsa_debug_int_pipe_rate")
+    return out.value
 
 
 def debug_set_cluster(ctas: int):
