@@ -49,6 +49,9 @@ WORKLOADS = {
     "plain1k": "plain family: k=1,000, root length 250, clip 50-400, seed 1",
     "scale400k": "scale family: k=400,000, root length log-normal (median 250, sigma 0.5) "
                  "clamped 30-3,000, 1% X/B/Z ambiguity residues, 25-letter alphabet, seed 1",
+    "batch512": "batched: 512 independent families, k log-uniform 50-5,000, root length "
+                "log-uniform 30-2,000, 0.02 subs/site and 0.01 indels/site per branch, seed 1; "
+                "one famsa_batch_pack + famsa_batch_tree (one CUDA graph) per step",
 }
 
 
@@ -60,6 +63,9 @@ def make_family(workload: str, seed: int, k: int | None):
         return synth.plain1k(seed)
     if workload == "scale400k":
         return synth.scale400k(seed, **({"k": k} if k else {}))
+    if workload == "batch512":  # one family stands for the batch (the oracle arm samples its rows)
+        fams = synth.batch512(seed)
+        return max(fams, key=lambda t: cells_and_pairs(t[1])[0])
     raise SystemExit("unknown workload %s" % workload)
 
 
@@ -155,7 +161,7 @@ def cpu_baseline(res, off, budget_s=15.0):
     prefix = np.concatenate([[0], np.cumsum(lens)])
     # grow the trailing-row sample until one run takes at least half the budget
     # (small samples under-use the host threads, so their rate is not extrapolated)
-    rows = 4
+    rows = 1
     while True:
         r0 = k - rows
         t0 = time.perf_counter()
@@ -211,6 +217,182 @@ def run_reference(args, rank, world):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def concat_families(fams):
+    res = np.concatenate([r for r, _ in fams])
+    offs, fo, base = [np.zeros(1, np.int64)], [0], 0
+    for r, o in fams:
+        offs.append(o[1:] + base)
+        base += int(o[-1])
+        fo.append(fo[-1] + len(o) - 1)
+    return res, np.concatenate(offs), np.array(fo, np.int64)
+
+
+def run_batch(args, rank, world, local_rank):
+    """Batched families: every step packs the whole batch and builds every tree
+    through one CUDA graph; the same families one plain pack + tree at a time
+    are timed beside it."""
+    import torch
+    import paper_1603_06958_gb300 as fg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    fg.load()
+    fams = synth.batch512(args.seed + rank)
+    res, off, fo = concat_families(fams)
+    cells = sum(cells_and_pairs(o)[0] for _, o in fams)
+    pairs = sum(cells_and_pairs(o)[1] for _, o in fams)
+    dres = torch.from_numpy(res).cuda()
+    doff = torch.from_numpy(off).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        b = fg.batch_pack(dres, doff, fo)
+        t = fg.batch_tree(b, device=True)
+        return b, t
+
+    for _ in range(args.warmup):
+        b, _ = step()
+        b.free()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, graph_ms, stats = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        b, _ = step()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(b.stats())
+        # the same graph again: the steady state of a resident batch
+        flush.zero_()
+        e1.record()
+        fg.batch_tree(b, device=True)
+        e2.record()
+        e2.synchronize()
+        graph_ms.append(e1.elapsed_time(e2))
+        b.free()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = float(np.mean(ms))
+    st = stats[-1]
+    lcs_ms = float(np.mean([s["lcs_ns"] for s in stats])) / 1e6
+
+    # plain: the same families, one famsa_pack_peq + famsa_slink_tree each
+    plain_ms = None
+    if not args.no_plain:
+        fams_dev = [(torch.from_numpy(r).cuda(), torch.from_numpy(o).cuda()) for r, o in fams]
+        for r, o in fams_dev[:8]:
+            fam = fg.pack_peq(r, o)
+            fg.slink_tree(fam, device=True)
+            fam.free()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r, o in fams_dev:
+            fam = fg.pack_peq(r, o)
+            fg.slink_tree(fam, device=True)
+            fam.free()
+        e1.record()
+        e1.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+
+    # end to end through the public API with pinned host buffers
+    pres = torch.from_numpy(res).pin_memory()
+    poff = torch.from_numpy(off).pin_memory()
+    e2e_ms = []
+    for i in range(1 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = fg.batch_pack(pres, poff, fo)
+        t = fg.batch_tree(b, device=False)
+        b.free()
+        dt = time.perf_counter() - t0
+        if i >= 1:
+            e2e_ms.append(1e3 * dt)
+    d2h = sum(v.nbytes for v in t.values())
+    h2d = res.nbytes + off.nbytes
+    if dist is not None:
+        vals = torch.tensor([ms_step, float(np.mean(e2e_ms)), cells], dtype=torch.float64, device="cuda")
+        mx = vals.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = vals.clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms_max, e2e_max, cells_total = float(mx[0]), float(mx[1]), float(tot[2])
+    else:
+        ms_max, e2e_max, cells_total = ms_step, float(np.mean(e2e_ms)), cells
+    if rank != 0:
+        return 0
+    achieved = OPS_PER_WORD_STEP * st["word_steps"] / (lcs_ms * 1e-3) / 1e12
+    peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9 / 1e12
+    line = {
+        "metric": METRIC, "value": cells_total / (ms_max * 1e-3) / 1e9, "unit": "GCUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["batch512"], "families": len(fams), "sequences": int(fo[-1]),
+                   "cells": cells, "pairs": pairs, "pairs_per_s": pairs * world / (ms_max * 1e-3),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between timed steps (L2 flush)",
+                   "inputs": "residues and offsets resident in HBM before each timed step",
+                   "breakdown_ms": {"lcs_kernels": lcs_ms,
+                                    "row_update_kernels": float(np.mean([s["update_ns"] for s in stats])) / 1e6,
+                                    "finalise": float(np.mean([s["finalize_ns"] for s in stats])) / 1e6,
+                                    "graph_only": float(np.mean(graph_ms))},
+                   "graph_only_gcups": cells / (float(np.mean(graph_ms)) * 1e-3) / 1e9,
+                   "plain_ms": plain_ms,
+                   "plain_gcups": (cells / (plain_ms * 1e-3) / 1e9) if plain_ms else None,
+                   "speedup_vs_plain": (plain_ms / ms_step) if plain_ms else None,
+                   "lcs_items": st["lcs_items"], "lcs_widths": st["lcs_widths"]},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_lcs_tpp / k_lcs_wpp over the batch work lists",
+                     "peak_note": "152 SMs x 64 ALU-pipe lanes x 2.07 GHz (bench.py --int-peaks)",
+                     "achieved_note": "6 INT32 ops per word step x word steps / LCS span of the graph "
+                                      "(CUDA events recorded inside the graph)"},
+        "e2e": {"value": cells_total / (e2e_max * 1e-3) / 1e9, "unit": "GCUPS",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(st["graph_launches"]) + 40,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_families(fams, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_families(fams, budget_s=15.0):
+    """The oracle's DP LCS over whole families of the batch, smallest first, until
+    about the budget is spent."""
+    import oracle
+    order = sorted(range(len(fams)), key=lambda f: cells_and_pairs(fams[f][1])[0])
+    done_cells, t_used, n = 0.0, 0.0, 0
+    for f in order:
+        r, o = fams[f]
+        c = cells_and_pairs(o)[0]
+        if n > 0 and t_used > 0 and (t_used + c * t_used / done_cells) > budget_s:
+            break
+        t0 = time.perf_counter()
+        oracle.lcs_allpairs(r, o)
+        t_used += time.perf_counter() - t0
+        done_cells += c
+        n += 1
+    return {"value": done_cells / t_used / 1e9, "unit": "GCUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "DP LCS of all pairs of the %d smallest families of the batch (%.3g cells, %.1f s)"
+                      % (n, done_cells, t_used)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -380,6 +562,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=int, default=12)
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batch512: skip timing the one-family-at-a-time comparator")
     ap.add_argument("--int-peaks", action="store_true",
                     help="measure the integer pipe widths used by the roofline, then exit")
     args = ap.parse_args()
@@ -397,7 +581,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    rc = run_ours(args, rank, world, local_rank)
+    rc = (run_batch if args.workload == "batch512" else run_ours)(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
