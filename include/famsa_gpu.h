@@ -193,6 +193,56 @@ int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_of
 int famsa_lcs_query_noalloc(const famsa_family *f, const uint8_t *q, const int64_t *q_offsets,
                             int32_t nq, int32_t max_len, int32_t *out, void *cuda_stream);
 
+/*
+ * Batched families -- the same stages I+II ("Pairwise similarities
+ * calculation", "Determination of the guide tree") for many independent
+ * families at once, so that small families do not leave the GPU idle.
+ *
+ * famsa_batch_pack -- validate and pack n_families families given as one
+ * sequence list (the family format with n_seqs sequences) split by
+ * family_offsets[n_families + 1] (HOST int64): family f is sequences
+ * family_offsets[f] .. family_offsets[f+1]-1, at least one each,
+ * family_offsets[0] = 0 and family_offsets[n_families] = n_seqs.
+ * residues/offsets are on the device iff residues_on_device != 0.
+ * Limits: n_seqs < 2^31, n_families <= 65535.  Errors: EINVAL, ERANGE,
+ * ENOMEM, ECUDA.  Synchronises cuda_stream.
+ */
+typedef struct famsa_batch famsa_batch;
+int famsa_batch_pack(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs,
+                     const int64_t *family_offsets, int32_t n_families, int residues_on_device,
+                     void *cuda_stream, famsa_batch **out);
+
+/*
+ * famsa_batch_tree -- every family's single-linkage tree, exactly as
+ * famsa_slink_tree gives it for that family alone, in the family's own
+ * labels 0..k_f-1:
+ *   pi, lambda_num, lambda_den: n_seqs entries; family f's at
+ *     family_offsets[f];
+ *   merges (2 per merge), h_num, h_den, sizes: n_seqs - n_families merges;
+ *     family f's k_f - 1 merges start at merge family_offsets[f] - f, with
+ *     cluster ids k_f + t local to the family.
+ * Any output may be NULL.  Outputs on the device iff out_on_device != 0.
+ * The first call builds the execution plan (work lists, buffers) and
+ * captures the whole computation -- LCS launches per kernel width over all
+ * families, the row update with one thread-block cluster per family, the
+ * finalisation -- into one CUDA graph; every call launches that graph on
+ * cuda_stream.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int famsa_batch_tree(famsa_batch *b, int32_t *pi, uint64_t *lambda_num, uint32_t *lambda_den,
+                     int32_t *merges, uint64_t *h_num, uint32_t *h_den, int32_t *sizes,
+                     int out_on_device, void *cuda_stream);
+
+/* Counters of the batch plan, stats[12] int64: 0 LCS cells (sum of |A||B|
+ * over every family's pairs), 1 LCS word steps, 2 pairs, 3 LCS work items,
+ * 4 kernel launches captured in the graph, 5 LCS kernel widths, 6 families
+ * on the global-memory row update, 7..9 device time in ns of the LCS, the
+ * row update and the finalisation in the last graph launch (this call waits
+ * for that launch), 10..11 reserved.  Zero before the first tree. */
+int famsa_batch_stats(const famsa_batch *b, int64_t *stats);
+
+/* Release a batch and its device memory (NULL is ignored). */
+void famsa_batch_free(famsa_batch *b);
+
 /* Release a handle and its device memory (NULL is ignored).  Waits for the
  * handle's pending work. */
 void famsa_free(famsa_family *f);

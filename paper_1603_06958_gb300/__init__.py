@@ -72,6 +72,11 @@ def load(path: str = LIB_PATH):
             "famsa_slink_tree": ([_P, _P, u64p, _P, _P, u64p, _P, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_lcs_query": ([_P, _P, _P, i32, ctypes.c_int, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_lcs_query_noalloc": ([_P, _P, _P, i32, i32, _P, _P], ctypes.c_int),
+            "famsa_batch_pack": ([_P, _P, ctypes.c_int64, _P, i32, ctypes.c_int, _P, ctypes.POINTER(_P)],
+                                 ctypes.c_int),
+            "famsa_batch_tree": ([_P, _P, u64p, _P, _P, u64p, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_batch_stats": ([_P, _P], ctypes.c_int),
+            "famsa_batch_free": ([_P], None),
             "famsa_free": ([_P], None),
             "famsa_last_stats": ([_P, _P], ctypes.c_int),
             "famsa_debug_fail_alloc_after": ([ctypes.c_int], ctypes.c_int),
@@ -243,6 +248,84 @@ def famsa_slink_tree(fam: Family, device: bool = False, stream=None) -> dict:
 
 
 slink_tree = famsa_slink_tree
+
+
+class Batch:
+    """Packed families resident on the device (owns the C batch handle)."""
+
+    def __init__(self, handle: int, family_offsets: np.ndarray):
+        self.handle = handle
+        self.family_offsets = family_offsets
+        self.n_seqs = int(family_offsets[-1])
+        self.n_families = len(family_offsets) - 1
+
+    def free(self):
+        if self.handle:
+            load().famsa_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = np.zeros(12, dtype=np.int64)
+        _check(load().famsa_batch_stats(self.handle, s.ctypes.data), "famsa_batch_stats")
+        keys = ["cells", "word_steps", "pairs", "lcs_items", "graph_launches", "lcs_widths",
+                "global_update_families", "lcs_ns", "update_ns", "finalize_ns"]
+        return {k: int(v) for k, v in zip(keys, s)}
+
+
+def famsa_batch_pack(residues, offsets, family_offsets, stream=None) -> Batch:
+    """Pack many families (one sequence list split by host family_offsets)."""
+    rp, rdev = _ptr(residues)
+    op, odev = _ptr(offsets)
+    if rdev != odev:
+        raise ValueError("residues and offsets must be on the same side")
+    fo = np.ascontiguousarray(np.asarray(family_offsets, dtype=np.int64))
+    n_seqs = len(offsets) - 1
+    h = _P()
+    _check(load().famsa_batch_pack(rp, op, n_seqs, fo.ctypes.data, len(fo) - 1, int(rdev),
+                                   _stream_ptr(stream), ctypes.byref(h)), "famsa_batch_pack")
+    return Batch(h.value, fo)
+
+
+batch_pack = famsa_batch_pack
+
+
+def famsa_batch_tree(b: Batch, device: bool = False, stream=None) -> dict:
+    """Every family's tree, concatenated (see the C header): pi/lambda per
+    sequence, merges per family at merge offset family_offsets[f] - f."""
+    n, m = b.n_seqs, b.n_seqs - b.n_families
+    out = {
+        "pi": _empty(n, np.int32, device),
+        "lambda_num": _empty(n, np.uint64, device),
+        "lambda_den": _empty(n, np.uint32, device),
+        "merges": _empty(2 * m, np.int32, device),
+        "h_num": _empty(m, np.uint64, device),
+        "h_den": _empty(m, np.uint32, device),
+        "sizes": _empty(m, np.int32, device),
+    }
+    ptrs = [_ptr(out[k])[0] for k in ("pi", "lambda_num", "lambda_den", "merges", "h_num", "h_den",
+                                      "sizes")]
+    _check(load().famsa_batch_tree(b.handle, *ptrs, int(device), _stream_ptr(stream)),
+           "famsa_batch_tree")
+    out["merges"] = out["merges"].reshape(m, 2)
+    return out
+
+
+batch_tree = famsa_batch_tree
+
+
+def batch_family_tree(out: dict, b: Batch, f: int) -> dict:
+    """Family f's slice of a famsa_batch_tree result."""
+    a, z = int(b.family_offsets[f]), int(b.family_offsets[f + 1])
+    ma, mz = a - f, z - f - 1
+    return {"pi": out["pi"][a:z], "lambda_num": out["lambda_num"][a:z],
+            "lambda_den": out["lambda_den"][a:z], "merges": out["merges"][ma:mz],
+            "h_num": out["h_num"][ma:mz], "h_den": out["h_den"][ma:mz], "sizes": out["sizes"][ma:mz]}
 
 
 def famsa_lcs_query(fam: Family, q_residues, q_offsets, out=None, device: bool = False,

@@ -1,0 +1,746 @@
+// Batched families: many independent families packed side by side and built
+// into guide trees by one CUDA graph.
+//
+// FAMSA Methods, "Pairwise similarities calculation" and "Determination of
+// the guide tree", applied to every family of a batch at once.  The families
+// share one length-sorted layout in which each family's block of sorted
+// positions is padded to a multiple of 32, so no 32-sequence column group
+// mixes families.  The LCS kernels then run over explicit work lists, one
+// launch per kernel width, covering the lower triangle of every family:
+// small families no longer leave the GPU idle between launches.  The 16-bit
+// rows of each family stay in HBM, and the row update runs one cluster per
+// family (state in that cluster's shared memory), all families of one
+// cluster size in one launch.  The finalisation gives each family's pointer
+// representation and merge list in that family's own labels.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "lcs_kernels.cuh"
+#include "slink_common.cuh"
+
+namespace famsa {
+
+// packing kernels shared with the single-family path (pack.cu)
+__global__ void k_lengths(const int64_t *off, int32_t k, int64_t base, int32_t *len, int64_t *off0,
+                          int *status, int *max_len);
+__global__ void k_codes(const uint8_t *res, int64_t n, int *status);
+__global__ void k_merge_pass(const uint64_t *in, uint64_t *out, int32_t n, int32_t width);
+__global__ void k_scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t *total);
+__global__ void k_pack_peq(const uint8_t *res, const int64_t *off, const int32_t *map,
+                           const int64_t *peq_off, int32_t n, uint32_t *peq);
+__global__ void k_col_layout(const uint8_t *res, const int64_t *off, const int32_t *perm,
+                             const int32_t *slen, int32_t k, const int64_t *group_off,
+                             const int32_t *group_chunks, uint8_t *colres);
+
+// sort key (family, length, index): 16 + 16 + 32 bits
+__global__ void k_batch_keys(const int32_t *len, const int64_t *fam_off, int32_t F, int32_t N,
+                             uint64_t *keys) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int32_t lo = 0, hi = F - 1;  // the family holding sequence i
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (fam_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  keys[i] = ((uint64_t)lo << 48) | ((uint64_t)(uint32_t)len[i] << 32) | (uint32_t)i;
+}
+
+// sorted rank s -> padded position S[f] + (s - fam_off[f]); pads keep perm -1, length 0
+__global__ void k_batch_fields(const uint64_t *keys, int32_t N, const int64_t *fam_off,
+                               const int64_t *S, int32_t *perm, int32_t *perm_local,
+                               int32_t *slen, int64_t *words) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const uint64_t key = keys[s];
+  const int32_t f = (int32_t)(key >> 48);
+  const int32_t l = (int32_t)((key >> 32) & 0xffffu);
+  const int32_t idx = (int32_t)(key & 0xffffffffu);
+  const int64_t P = S[f] + (s - fam_off[f]);
+  perm[P] = idx;
+  perm_local[P] = (int32_t)(idx - fam_off[f]);
+  slen[P] = l;
+  words[P] = (l + 63) / 64;
+}
+
+__global__ void k_batch_group_sizes(const int32_t *slen, int32_t n_groups, int32_t *chunks,
+                                    int64_t *bytes) {
+  const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_groups) return;
+  int32_t mx = 0;
+  for (int j = 0; j < kGroup; ++j) mx = max(mx, slen[(int64_t)g * kGroup + j]);
+  const int32_t c = (mx + kChunk - 1) / kChunk;
+  chunks[g] = c;
+  bytes[g] = (int64_t)c * kGroup * kChunk;
+}
+
+// the layout of one point (point 0) in buffer 1 of every family's state, and
+// the outputs of single-point families
+struct BatchInit {
+  int32_t *ord1, *olen1, *pi1;
+  uint64_t *lam1;
+  uint64_t inf;          // +inf in the key packing of the family's row-update kernel
+  int32_t len0;
+  int32_t single;        // 1: the family is one point
+  int64_t out_at;        // its output position
+};
+__global__ void k_batch_init(const BatchInit *d, int32_t n, int32_t *pi_out, uint64_t *lnum_out,
+                             uint32_t *lden_out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BatchInit b = d[i];
+  if (b.single) {
+    pi_out[b.out_at] = 0;
+    lnum_out[b.out_at] = 1;
+    lden_out[b.out_at] = 0;
+    return;
+  }
+  b.ord1[0] = 0;
+  b.olen1[0] = b.len0;
+  b.lam1[0] = b.inf;
+  b.pi1[0] = 0;
+}
+
+struct Batch {
+  int device = 0;
+  int32_t F = 0, N = 0;
+  int64_t Kpad = 0;
+  int32_t max_len = 0;
+  std::vector<int64_t> fam_off, S;  // F+1 each
+  std::vector<int32_t> h_slen;      // Kpad
+  uint8_t *d_res = nullptr;
+  int64_t *d_off = nullptr, *d_fam_off = nullptr, *d_S = nullptr;
+  int32_t *d_len = nullptr, *d_perm = nullptr, *d_perm_local = nullptr, *d_slen = nullptr;
+  int64_t *d_peq_off = nullptr;
+  uint32_t *d_peq = nullptr;
+  int32_t n_groups = 0;
+  int64_t *d_group_off = nullptr;
+  int32_t *d_group_chunks = nullptr;
+  uint8_t *d_colres = nullptr;
+  // execution plan (built by the first tree call)
+  bool planned = false;
+  std::vector<void *> plan_mem;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
+  cudaGraphExec_t exec = nullptr;
+  int32_t *d_pi = nullptr, *d_merges = nullptr, *d_sizes = nullptr;
+  uint64_t *d_lnum = nullptr, *d_hnum = nullptr;
+  uint32_t *d_lden = nullptr, *d_hden = nullptr;
+  // graph start, LCS, update, end: recorded by event-record nodes of the graph
+  cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool launched = false;
+  int64_t stats[12] = {0};
+  std::mutex mu;
+};
+
+static void batch_free_plan(Batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  for (auto e : b->ev) cudaEventDestroy(e);
+  b->ev.clear();
+  for (auto &e : b->tev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  b->launched = false;
+  for (auto s : b->side) cudaStreamDestroy(s);
+  b->side.clear();
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->cap = nullptr;
+  for (void *p : b->plan_mem) dev_free(p);
+  b->plan_mem.clear();
+  b->planned = false;
+}
+
+static void batch_free(Batch *b) {
+  if (!b) return;
+  batch_free_plan(b);
+  dev_free(b->d_res); dev_free(b->d_off); dev_free(b->d_fam_off); dev_free(b->d_S);
+  dev_free(b->d_len); dev_free(b->d_perm); dev_free(b->d_perm_local); dev_free(b->d_slen);
+  dev_free(b->d_peq_off); dev_free(b->d_peq); dev_free(b->d_group_off);
+  dev_free(b->d_group_chunks); dev_free(b->d_colres);
+  delete b;
+}
+
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+#define BCK(x)                                          \
+  do {                                                  \
+    cudaError_t e_ = (x);                               \
+    if (e_ != cudaSuccess) { err = e_; goto fail; }     \
+  } while (0)
+
+static int batch_pack(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs,
+                      const int64_t *fam_off, int32_t F, bool on_device, cudaStream_t st,
+                      Batch **out) {
+  *out = nullptr;
+  if (n_seqs < 1 || n_seqs >= (1ll << 31) || F < 1 || F > 65535 || !fam_off) return FAMSA_EINVAL;
+  if (fam_off[0] != 0 || fam_off[F] != n_seqs) return FAMSA_EINVAL;
+  for (int32_t f = 0; f < F; ++f)
+    if (fam_off[f + 1] <= fam_off[f]) return FAMSA_EINVAL;
+  const int32_t N = (int32_t)n_seqs;
+  AllocStream alloc_on(st);
+  Batch *b = new Batch();
+  cudaError_t err = cudaSuccess;
+  cudaGetDevice(&b->device);
+  b->F = F;
+  b->N = N;
+  b->fam_off.assign(fam_off, fam_off + F + 1);
+  b->S.resize(F + 1);
+  b->S[0] = 0;
+  for (int32_t f = 0; f < F; ++f)
+    b->S[f + 1] = b->S[f] + ((fam_off[f + 1] - fam_off[f] + kGroup - 1) / kGroup) * kGroup;
+  b->Kpad = b->S[F];
+  b->n_groups = (int32_t)(b->Kpad / kGroup);
+  const int T = 256;
+  int64_t base = 0, total = 0;
+  int64_t *d_off_in = nullptr, *words = nullptr, *gbytes = nullptr, *d_tot = nullptr;
+  uint64_t *keys = nullptr, *keys2 = nullptr;
+  int *d_status = nullptr;
+  int h_status[2] = {0, 0};
+  int64_t h_tot[2] = {0, 0};
+  if (on_device) {
+    int64_t ends[2];
+    BCK(cudaMemcpyAsync(&ends[0], offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BCK(cudaMemcpyAsync(&ends[1], offsets + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    base = ends[0];
+    total = ends[1] - ends[0];
+    d_off_in = const_cast<int64_t *>(offsets);
+  } else {
+    for (int32_t i = 0; i < N; ++i)
+      if (offsets[i + 1] <= offsets[i]) { batch_free(b); return FAMSA_EINVAL; }
+    for (int32_t i = 0; i < N; ++i)
+      if (offsets[i + 1] - offsets[i] > kMaxLen) { batch_free(b); return FAMSA_ERANGE; }
+    base = offsets[0];
+    total = offsets[N] - offsets[0];
+  }
+  if (base < 0 || total < N) { batch_free(b); return FAMSA_EINVAL; }
+  BCK(dev_alloc((void **)&b->d_off, sizeof(int64_t) * (N + 1)));
+  BCK(dev_alloc((void **)&b->d_res, (size_t)total));
+  BCK(dev_alloc((void **)&b->d_len, sizeof(int32_t) * N));
+  BCK(dev_alloc((void **)&d_status, sizeof(int) * 2));
+  BCK(cudaMemsetAsync(d_status, 0, sizeof(int) * 2, st));
+  if (on_device) {
+    BCK(cudaMemcpyAsync(b->d_res, residues + base, (size_t)total, cudaMemcpyDeviceToDevice, st));
+  } else {
+    BCK(dev_alloc((void **)&d_off_in, sizeof(int64_t) * (N + 1)));
+    BCK(cudaMemcpyAsync(d_off_in, offsets, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(b->d_res, residues + base, (size_t)total, cudaMemcpyHostToDevice, st));
+  }
+  k_lengths<<<nblk(N + 1, T), T, 0, st>>>(d_off_in, N, base, b->d_len, b->d_off, d_status,
+                                          d_status + 1);
+  k_codes<<<std::min<int64_t>(nblk(total, T), 4096), T, 0, st>>>(b->d_res, total, d_status);
+  BCK(cudaGetLastError());
+  BCK(cudaMemcpyAsync(h_status, d_status, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  if (!on_device) { dev_free(d_off_in); d_off_in = nullptr; }
+  if (h_status[0]) {
+    dev_free(d_status);
+    batch_free(b);
+    return (h_status[0] & kTooLong) ? FAMSA_ERANGE : FAMSA_EINVAL;
+  }
+  b->max_len = h_status[1];
+
+  // sort by (family, length, index), then the padded sorted layout
+  BCK(dev_alloc((void **)&b->d_fam_off, sizeof(int64_t) * (F + 1)));
+  BCK(dev_alloc((void **)&b->d_S, sizeof(int64_t) * (F + 1)));
+  BCK(cudaMemcpyAsync(b->d_fam_off, fam_off, sizeof(int64_t) * (F + 1), cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(b->d_S, b->S.data(), sizeof(int64_t) * (F + 1), cudaMemcpyHostToDevice, st));
+  BCK(dev_alloc((void **)&keys, sizeof(uint64_t) * N));
+  BCK(dev_alloc((void **)&keys2, sizeof(uint64_t) * N));
+  k_batch_keys<<<nblk(N, T), T, 0, st>>>(b->d_len, b->d_fam_off, F, N, keys);
+  for (int64_t width = 1; width < N; width *= 2) {
+    k_merge_pass<<<nblk(N, T), T, 0, st>>>(keys, keys2, N, (int32_t)width);
+    std::swap(keys, keys2);
+  }
+  BCK(dev_alloc((void **)&b->d_perm, sizeof(int32_t) * b->Kpad));
+  BCK(dev_alloc((void **)&b->d_perm_local, sizeof(int32_t) * b->Kpad));
+  BCK(dev_alloc((void **)&b->d_slen, sizeof(int32_t) * b->Kpad));
+  BCK(dev_alloc((void **)&b->d_peq_off, sizeof(int64_t) * (b->Kpad + 1)));
+  BCK(dev_alloc((void **)&words, sizeof(int64_t) * (b->Kpad + 1)));
+  BCK(dev_alloc((void **)&d_tot, sizeof(int64_t) * 2));
+  BCK(cudaMemsetAsync(b->d_perm, 0xff, sizeof(int32_t) * b->Kpad, st));
+  BCK(cudaMemsetAsync(b->d_perm_local, 0xff, sizeof(int32_t) * b->Kpad, st));
+  BCK(cudaMemsetAsync(b->d_slen, 0, sizeof(int32_t) * b->Kpad, st));
+  BCK(cudaMemsetAsync(words, 0, sizeof(int64_t) * (b->Kpad + 1), st));
+  k_batch_fields<<<nblk(N, T), T, 0, st>>>(keys, N, b->d_fam_off, b->d_S, b->d_perm,
+                                           b->d_perm_local, b->d_slen, words);
+  k_scan_excl<<<1, 1024, 0, st>>>(words, b->d_peq_off, b->Kpad, d_tot);
+  BCK(cudaGetLastError());
+  BCK(dev_alloc((void **)&b->d_group_chunks, sizeof(int32_t) * b->n_groups));
+  BCK(dev_alloc((void **)&b->d_group_off, sizeof(int64_t) * (b->n_groups + 1)));
+  BCK(dev_alloc((void **)&gbytes, sizeof(int64_t) * b->n_groups));
+  k_batch_group_sizes<<<nblk(b->n_groups, T), T, 0, st>>>(b->d_slen, b->n_groups, b->d_group_chunks,
+                                                          gbytes);
+  k_scan_excl<<<1, 1024, 0, st>>>(gbytes, b->d_group_off, b->n_groups, d_tot + 1);
+  BCK(cudaGetLastError());
+  BCK(cudaMemcpyAsync(h_tot, d_tot, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, st));
+  b->h_slen.resize(b->Kpad);
+  BCK(cudaMemcpyAsync(b->h_slen.data(), b->d_slen, sizeof(int32_t) * b->Kpad, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  BCK(cudaMemcpyAsync(b->d_peq_off + b->Kpad, &d_tot[0], sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  BCK(cudaMemcpyAsync(b->d_group_off + b->n_groups, &d_tot[1], sizeof(int64_t),
+                      cudaMemcpyDeviceToDevice, st));
+  BCK(dev_alloc((void **)&b->d_peq, sizeof(uint32_t) * kPeqWordU32 * (size_t)std::max<int64_t>(h_tot[0], 1)));
+  BCK(dev_alloc((void **)&b->d_colres, (size_t)std::max<int64_t>(h_tot[1], 16)));
+  k_pack_peq<<<nblk(b->Kpad * 32, T), T, 0, st>>>(b->d_res, b->d_off, b->d_perm, b->d_peq_off,
+                                                  (int32_t)b->Kpad, b->d_peq);
+  k_col_layout<<<b->n_groups, 256, 0, st>>>(b->d_res, b->d_off, b->d_perm, b->d_slen,
+                                            (int32_t)b->Kpad, b->d_group_off, b->d_group_chunks,
+                                            b->d_colres);
+  BCK(cudaGetLastError());
+  BCK(cudaStreamSynchronize(st));
+  dev_free(keys); dev_free(keys2); dev_free(words); dev_free(gbytes); dev_free(d_tot);
+  dev_free(d_status);
+  *out = b;
+  return FAMSA_OK;
+
+fail:
+  cudaStreamSynchronize(st);
+  if (!on_device) dev_free(d_off_in);
+  dev_free(keys); dev_free(keys2); dev_free(words); dev_free(gbytes); dev_free(d_tot);
+  dev_free(d_status);
+  batch_free(b);
+  return status_from_cuda(err);
+}
+
+// ---------------------------------------------------------------- the plan
+struct Arena {
+  std::vector<void *> *mem;
+  cudaError_t err = cudaSuccess;
+  template <typename T>
+  T *get(size_t n) {
+    void *p = nullptr;
+    if (err != cudaSuccess) return nullptr;
+    err = dev_alloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (err != cudaSuccess) return nullptr;
+    mem->push_back(p);
+    return static_cast<T *>(p);
+  }
+};
+
+template <typename T>
+static cudaError_t upload_vec(Arena &A, const std::vector<T> &v, T **d, cudaStream_t st) {
+  *d = A.get<T>(v.size());
+  if (A.err != cudaSuccess) return A.err;
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+}
+
+static int tpp_R(int W) { return W <= 4 ? 4 : (W <= 8 ? 2 : 1); }
+static int wpp_NW(int W) {
+  int nw = 1;
+  while (32 * nw < W) nw *= 2;
+  return nw;
+}
+
+struct Bucket {
+  bool wpp;
+  int kw;  // W (thread-per-pair) or NW (warp-per-pair)
+  std::vector<int4> items;
+};
+
+static int batch_plan(Batch *b, cudaStream_t st) {
+  AllocStream alloc_on(st);
+  const int32_t F = b->F;
+  Arena A{&b->plan_mem};
+  cudaError_t err = cudaSuccess;
+  const int T = 256;
+  // per-family sizes and row blocks (rows 1..k-1 of each family, its own leading dimension)
+  std::vector<int64_t> rb_off(F + 1, 0), ld(F);
+  for (int32_t f = 0; f < F; ++f) {
+    const int64_t k = b->fam_off[f + 1] - b->fam_off[f];
+    ld[f] = (k + 1) & ~1ll;
+    rb_off[f + 1] = rb_off[f] + (k - 1) * ld[f];
+  }
+  // row entries, grouped by kernel width; within a width, family by family
+  std::vector<Bucket> buckets;
+  std::vector<int> bucket_of(64 + 7, -1);
+  auto bucket_for = [&](int W) -> int {
+    const bool wpp = W > kTppMaxW;
+    const int key = wpp ? 33 + __builtin_ctz(wpp_NW(W)) : W;
+    if (bucket_of[key] < 0) {
+      bucket_of[key] = (int)buckets.size();
+      buckets.push_back(Bucket{wpp, wpp ? wpp_NW(W) : W, {}});
+    }
+    return bucket_of[key];
+  };
+  std::vector<std::vector<int64_t>> e_peq(1), e_base(1);
+  std::vector<std::vector<int32_t>> e_len(1), e_id(1);
+  // first pass: which rows go to which bucket, in order
+  struct Row { int32_t rid; int32_t f; };
+  std::vector<std::vector<Row>> rows_by_bucket;
+  int64_t cells = 0, words = 0, pairs = 0;
+  std::vector<int64_t> h_peq_off(b->Kpad + 1, 0);
+  for (int64_t s = 0; s < b->Kpad; ++s) h_peq_off[s + 1] = h_peq_off[s] + (b->h_slen[s] + 63) / 64;
+  for (int32_t f = 0; f < F; ++f) {
+    const int32_t k = (int32_t)(b->fam_off[f + 1] - b->fam_off[f]);
+    int64_t colsum = 0;
+    pairs += (int64_t)k * (k - 1) / 2;
+    for (int32_t n = 0; n < k; ++n) {
+      const int32_t rid = (int32_t)(b->S[f] + n);
+      const int32_t l = b->h_slen[rid];
+      const int W = (l + 63) / 64;
+      words += (int64_t)W * colsum;
+      cells += (int64_t)l * colsum;
+      colsum += l;
+      if (n == 0) continue;
+      const int bk = bucket_for(W);
+      if ((int)rows_by_bucket.size() <= bk) rows_by_bucket.resize(bk + 1);
+      rows_by_bucket[bk].push_back(Row{rid, f});
+    }
+  }
+  // second pass: row arrays and work items
+  std::vector<int64_t> r_peq, r_base;
+  std::vector<int32_t> r_len, r_id;
+  for (size_t bk = 0; bk < buckets.size(); ++bk) {
+    Bucket &B = buckets[bk];
+    const auto &rows = rows_by_bucket[bk];
+    const int R = B.wpp ? 1 : tpp_R(B.kw);
+    size_t i = 0;
+    while (i < rows.size()) {
+      const int32_t f = rows[i].f;
+      size_t j = i + 1;
+      while (j < rows.size() && j - i < (size_t)R && rows[j].f == f) ++j;
+      const int32_t e0 = (int32_t)r_id.size();
+      for (size_t q = i; q < j; ++q) {
+        const int32_t rid = rows[q].rid;
+        r_peq.push_back(h_peq_off[rid]);
+        r_len.push_back(b->h_slen[rid]);
+        r_id.push_back(rid);
+        r_base.push_back(rb_off[f] + (int64_t)(rid - b->S[f] - 1) * ld[f] - b->S[f]);
+      }
+      const int32_t rid_last = rows[j - 1].rid;
+      const int32_t g0 = (int32_t)(b->S[f] / kGroup);
+      if (!B.wpp) {
+        for (int32_t g = g0; g * kGroup < rid_last; g += 4) B.items.push_back(make_int4(e0, (int)(j - i), g, 0));
+      } else {
+        for (int32_t c = (int32_t)b->S[f]; c < rid_last; c += kWppCols)
+          B.items.push_back(make_int4(e0, 1, c / kGroup, 0));
+      }
+      i = j;
+    }
+  }
+  int64_t n_items = 0;
+  for (auto &B : buckets) n_items += (int64_t)B.items.size();
+  b->stats[0] = cells;
+  b->stats[1] = words;
+  b->stats[2] = pairs;
+  b->stats[3] = n_items;
+
+  // device copies of the row arrays and items
+  int64_t *d_rpeq = nullptr, *d_rbase = nullptr;
+  int32_t *d_rlen = nullptr, *d_rid = nullptr;
+  std::vector<int4> all_items;
+  std::vector<int64_t> item_off(buckets.size() + 1, 0);
+  for (size_t bk = 0; bk < buckets.size(); ++bk) {
+    item_off[bk + 1] = item_off[bk] + (int64_t)buckets[bk].items.size();
+    all_items.insert(all_items.end(), buckets[bk].items.begin(), buckets[bk].items.end());
+  }
+  int4 *d_items = nullptr;
+  uint16_t *rowbuf = nullptr;
+  std::vector<SmemArgs> smem_args[5];  // cluster sizes 1, 2, 4, 8, 16
+  int32_t smem_P[5] = {0, 0, 0, 0, 0};
+  struct GlobalFam { SlinkState S; int64_t off, ld; int32_t k; };
+  std::vector<GlobalFam> global_fams;
+  std::vector<BatchInit> inits;
+  struct FinJob { int32_t f, k; bool widen; const int32_t *ord; uint64_t *gap, *lam; FinBufs FB; };
+  std::vector<FinJob> fins;
+  const bool narrow = b->max_len <= 32767;
+  const uint64_t inf_narrow = KeysNarrow::kInf, inf_wide = KeysWide::kInf;
+  uint64_t *ctl_all = nullptr;
+  int64_t n_ctl = 0;
+  BatchInit *d_init = nullptr;
+  SmemArgs *d_sargs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const int max_cl = max_cluster_global();
+
+  BCK(upload_vec(A, r_peq, &d_rpeq, st));
+  BCK(upload_vec(A, r_base, &d_rbase, st));
+  BCK(upload_vec(A, r_len, &d_rlen, st));
+  BCK(upload_vec(A, r_id, &d_rid, st));
+  BCK(upload_vec(A, all_items, &d_items, st));
+  rowbuf = A.get<uint16_t>((size_t)rb_off[F]);
+  // outputs (whole batch)
+  b->d_pi = A.get<int32_t>(b->N);
+  b->d_lnum = A.get<uint64_t>(b->N);
+  b->d_lden = A.get<uint32_t>(b->N);
+  b->d_merges = A.get<int32_t>(2 * (size_t)(b->N - F));
+  b->d_hnum = A.get<uint64_t>(b->N - F);
+  b->d_hden = A.get<uint32_t>(b->N - F);
+  b->d_sizes = A.get<int32_t>(b->N - F);
+  for (int32_t f = 0; f < F; ++f) n_ctl += kCtlWords;
+  ctl_all = A.get<uint64_t>((size_t)n_ctl);
+  if (A.err != cudaSuccess) { err = A.err; goto fail; }
+
+  // per-family row-update state and finalisation buffers
+  for (int32_t f = 0; f < F; ++f) {
+    const int32_t k = (int32_t)(b->fam_off[f + 1] - b->fam_off[f]);
+    BatchInit in = {};
+    in.out_at = b->fam_off[f];
+    if (k == 1) {
+      in.single = 1;
+      inits.push_back(in);
+      continue;
+    }
+    SlinkState S = {};
+    const size_t kp = (size_t)k + 1;
+    for (int i = 0; i < 2; ++i) {
+      S.ord[i] = A.get<int32_t>(kp);
+      S.olen[i] = A.get<int32_t>(kp);
+      S.gap[i] = A.get<uint64_t>(kp);
+      S.lam[i] = A.get<uint64_t>(kp);
+      S.pi[i] = A.get<int32_t>(kp);
+      S.mD[i] = A.get<uint64_t>(kp);
+      S.mOrd[i] = A.get<int32_t>(kp);
+      S.mLen[i] = A.get<int32_t>(kp);
+      S.mOld[i] = A.get<int32_t>(kp);
+      S.mLam[i] = A.get<uint64_t>(kp);
+      S.mPi[i] = A.get<int32_t>(kp);
+      S.mRaw[i] = A.get<int32_t>(kp);
+    }
+    S.D = A.get<uint64_t>(kp);
+    S.mGap = A.get<uint64_t>(kp);
+    S.runsA = A.get<int32_t>(kp);
+    S.runsB = A.get<int32_t>(kp);
+    S.ctl = ctl_all + (size_t)f * kCtlWords;
+    S.slen = b->d_slen + b->S[f];
+    const int cl = smem_cluster_for(k, 0);
+    const bool smem = cl > 0 && cl <= max_cl;
+    in.ord1 = S.ord[1];
+    in.olen1 = S.olen[1];
+    in.pi1 = S.pi[1];
+    in.lam1 = S.lam[1];
+    in.len0 = b->h_slen[b->S[f]];
+    in.inf = (smem && narrow) ? inf_narrow : inf_wide;  // the global-memory kernel keeps wide keys
+    inits.push_back(in);
+    if (smem) {
+      const int ci = __builtin_ctz(cl);
+      SmemArgs a = {};
+      a.s = S;
+      a.rowbuf = rowbuf + rb_off[f];
+      a.ld = ld[f];
+      a.r0 = 1;
+      a.r1 = k;
+      a.P = (k + cl - 1) / cl;
+      a.batch = nullptr;
+      smem_args[ci].push_back(a);
+      smem_P[ci] = std::max(smem_P[ci], a.P);
+    } else {
+      global_fams.push_back(GlobalFam{S, rb_off[f], ld[f], k});
+    }
+    const size_t lv = fin_levels(k);
+    FinBufs FB = {};
+    FB.idx = A.get<int32_t>(k); FB.posof = A.get<int32_t>(k);
+    FB.it = A.get<int32_t>(lv * k); FB.rt = A.get<int32_t>(lv * k);
+    FB.gt = A.get<uint64_t>(lv * k);
+    FB.sub_lo = A.get<int32_t>(k); FB.sub_hi = A.get<int32_t>(k);
+    FB.ordA = A.get<int32_t>(k); FB.ordB = A.get<int32_t>(k); FB.rank = A.get<int32_t>(k);
+    FB.sorder = A.get<int32_t>(k);
+    FB.lam = A.get<uint64_t>(k); FB.hkey = A.get<uint64_t>(k);
+    FB.sz = A.get<int64_t>(k); FB.szpre = A.get<int64_t>(k); FB.tot = A.get<int64_t>(2);
+    const int64_t o = b->fam_off[f], om = b->fam_off[f] - f;
+    FB.pi = b->d_pi + o;
+    FB.lnum = b->d_lnum + o;
+    FB.lden = b->d_lden + o;
+    FB.merges = b->d_merges + 2 * om;
+    FB.hnum = b->d_hnum + om;
+    FB.hden = b->d_hden + om;
+    FB.sizes = b->d_sizes + om;
+    const int bk = k & 1;
+    fins.push_back(FinJob{f, k, smem && narrow, S.ord[bk], S.gap[bk], S.lam[bk], FB});
+  }
+  if (A.err != cudaSuccess) { err = A.err; goto fail; }
+  BCK(upload_vec(A, inits, &d_init, st));
+  for (int ci = 0; ci < 5; ++ci)
+    if (!smem_args[ci].empty()) BCK(upload_vec(A, smem_args[ci], &d_sargs[ci], st));
+  BCK(cudaStreamSynchronize(st));
+
+  // ---- capture the whole pipeline once
+  BCK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  b->side.resize(8);
+  for (auto &s : b->side) BCK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  b->ev.resize(1 + b->side.size());
+  for (auto &e : b->ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (auto &e : b->tev) BCK(cudaEventCreate(&e));
+  {
+    cudaGraph_t graph = nullptr;
+    int64_t launches = 0;
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    {
+      cudaError_t e = cudaEventRecordWithFlags(b->tev[0], b->cap, cudaEventRecordExternal);
+      // stage I: every family's triangle, one launch per kernel width
+      KParams p = {};
+      p.peq = b->d_peq;
+      p.row_peq_off = d_rpeq;
+      p.row_len = d_rlen;
+      p.row_id = d_rid;
+      p.row_orig = nullptr;
+      p.colres = b->d_colres;
+      p.group_off = b->d_group_off;
+      p.group_chunks = b->d_group_chunks;
+      p.col_perm = b->d_perm;
+      p.col_len = b->d_slen;
+      p.n_cols = (int32_t)b->Kpad;
+      p.n_groups = b->n_groups;
+      p.mode = kOutBatch;
+      p.out = rowbuf;
+      p.ld = 0;
+      p.row0 = 0;
+      p.k = 0;
+      p.triangle = 1;
+      p.row_base = d_rbase;
+      for (size_t bk = 0; bk < buckets.size() && e == cudaSuccess; ++bk) {
+        const int64_t n = item_off[bk + 1] - item_off[bk];
+        if (n == 0) continue;
+        p.items = d_items + item_off[bk];
+        p.e0 = 0;
+        p.e1 = (int32_t)r_id.size();
+        e = buckets[bk].wpp ? launch_wpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap)
+                            : launch_tpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap);
+        ++launches;
+      }
+      // stage II: one cluster per family
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[1], b->cap, cudaEventRecordExternal);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctl_all, 0, sizeof(uint64_t) * n_ctl, b->cap);
+      if (e == cudaSuccess && !inits.empty()) {
+        k_batch_init<<<nblk((int64_t)inits.size(), T), T, 0, b->cap>>>(
+            d_init, (int32_t)inits.size(), b->d_pi, b->d_lnum, b->d_lden);
+        e = cudaGetLastError();
+        ++launches;
+      }
+      for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
+        if (smem_args[ci].empty()) continue;
+        e = launch_slink_smem_batch(d_sargs[ci], (int32_t)smem_args[ci].size(), 1 << ci, smem_P[ci],
+                                    narrow, b->cap);
+        ++launches;
+      }
+      for (auto &g : global_fams) {
+        if (e != cudaSuccess) break;
+        e = launch_slink_global(g.S, rowbuf + g.off, g.ld, 1, g.k, max_cl, b->cap);
+        ++launches;
+      }
+      // finalisation, spread over side streams
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[2], b->cap, cudaEventRecordExternal);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->cap);
+      for (auto &s : b->side)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev[0], 0);
+      for (size_t j = 0; j < fins.size() && e == cudaSuccess; ++j) {
+        FinJob &J = fins[j];
+        cudaStream_t s = b->side[j % b->side.size()];
+        if (J.widen) {
+          e = widen_keys(J.gap, J.k - 1, s);
+          if (e == cudaSuccess) e = widen_keys(J.lam, J.k, s);
+          launches += 2;
+        }
+        if (e == cudaSuccess)
+          e = launch_finalize(J.ord, J.gap, b->d_perm_local + b->S[J.f], J.k, J.FB, s, &launches);
+      }
+      for (size_t i = 0; i < b->side.size() && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(b->ev[1 + i], b->side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev[1 + i], 0);
+      }
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[3], b->cap, cudaEventRecordExternal);
+      cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+      if (e == cudaSuccess) e = e2;
+      if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        err = e;
+        goto fail;
+      }
+    }
+    err = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) goto fail;
+    b->stats[4] = launches;
+    b->stats[5] = (int64_t)buckets.size();
+    b->stats[6] = (int64_t)global_fams.size();
+  }
+  b->planned = true;
+  return FAMSA_OK;
+
+fail:
+  cudaStreamSynchronize(st);
+  batch_free_plan(b);
+  return status_from_cuda(err);
+}
+
+}  // namespace famsa
+
+using namespace famsa;
+
+extern "C" {
+
+int famsa_batch_pack(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs,
+                     const int64_t *family_offsets, int32_t n_families, int residues_on_device,
+                     void *cuda_stream, famsa_batch **out) {
+  if (!out) return FAMSA_EINVAL;
+  *out = nullptr;
+  if (!residues || !offsets || !family_offsets) return FAMSA_EINVAL;
+  Batch *b = nullptr;
+  int rc = batch_pack(residues, offsets, n_seqs, family_offsets, n_families, residues_on_device != 0,
+                      (cudaStream_t)cuda_stream, &b);
+  if (rc != FAMSA_OK) return rc;
+  *out = reinterpret_cast<famsa_batch *>(b);
+  return FAMSA_OK;
+}
+
+int famsa_batch_tree(famsa_batch *bh, int32_t *pi, uint64_t *lambda_num, uint32_t *lambda_den,
+                     int32_t *merges, uint64_t *h_num, uint32_t *h_den, int32_t *sizes,
+                     int out_on_device, void *cuda_stream) {
+  if (!bh) return FAMSA_EINVAL;
+  Batch *b = reinterpret_cast<Batch *>(bh);
+  std::lock_guard<std::mutex> lk(b->mu);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!b->planned) {
+    int rc = batch_plan(b, st);
+    if (rc != FAMSA_OK) return rc;
+  }
+  cudaError_t err = cudaGraphLaunch(b->exec, st);
+  if (err == cudaSuccess) b->launched = true;
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t N = (size_t)b->N, M = (size_t)(b->N - b->F);
+  if (err == cudaSuccess && pi) err = cudaMemcpyAsync(pi, b->d_pi, sizeof(int32_t) * N, kind, st);
+  if (err == cudaSuccess && lambda_num)
+    err = cudaMemcpyAsync(lambda_num, b->d_lnum, sizeof(uint64_t) * N, kind, st);
+  if (err == cudaSuccess && lambda_den)
+    err = cudaMemcpyAsync(lambda_den, b->d_lden, sizeof(uint32_t) * N, kind, st);
+  if (M > 0) {
+    if (err == cudaSuccess && merges)
+      err = cudaMemcpyAsync(merges, b->d_merges, sizeof(int32_t) * 2 * M, kind, st);
+    if (err == cudaSuccess && h_num) err = cudaMemcpyAsync(h_num, b->d_hnum, sizeof(uint64_t) * M, kind, st);
+    if (err == cudaSuccess && h_den) err = cudaMemcpyAsync(h_den, b->d_hden, sizeof(uint32_t) * M, kind, st);
+    if (err == cudaSuccess && sizes) err = cudaMemcpyAsync(sizes, b->d_sizes, sizeof(int32_t) * M, kind, st);
+  }
+  if (err == cudaSuccess && !out_on_device) err = cudaStreamSynchronize(st);
+  return status_from_cuda(err);
+}
+
+int famsa_batch_stats(const famsa_batch *bh, int64_t *stats) {
+  if (!bh || !stats) return FAMSA_EINVAL;
+  Batch *b = const_cast<Batch *>(reinterpret_cast<const Batch *>(bh));
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->launched) {
+    // device time of the stages of the last graph launch (waits for it)
+    float ms[3] = {0.f, 0.f, 0.f};
+    cudaError_t err = cudaEventSynchronize(b->tev[3]);
+    for (int i = 0; i < 3 && err == cudaSuccess; ++i) err = cudaEventElapsedTime(&ms[i], b->tev[i], b->tev[i + 1]);
+    if (err != cudaSuccess) return status_from_cuda(err);
+    for (int i = 0; i < 3; ++i) b->stats[7 + i] = (int64_t)(ms[i] * 1e6);
+  }
+  for (int i = 0; i < 12; ++i) stats[i] = b->stats[i];
+  return FAMSA_OK;
+}
+
+void famsa_batch_free(famsa_batch *bh) {
+  if (!bh) return;
+  Batch *b = reinterpret_cast<Batch *>(bh);
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    cudaDeviceSynchronize();
+  }
+  batch_free(b);
+}
+
+}  // extern "C"

@@ -17,6 +17,7 @@ constexpr int kCodes = 25;          // residue codes 0..24
 constexpr int kCodeSlots = 32;      // Peq planes padded to 32 symbols (one bank per symbol)
 constexpr int kPadCode = 31;        // column padding symbol: its Peq is 0 in every row
 constexpr int kMaxLen = 65535;
+enum : int { kBadArg = 1, kTooLong = 2 };  // validation status bits of the packing kernels
 constexpr int kGroup = 32;          // columns per group (one warp)
 constexpr int kChunk = 16;          // residues per interleaved chunk (one 16-byte load)
 constexpr int kTppMaxW = 32;        // thread-per-pair handles rows of up to 32 words
@@ -79,8 +80,18 @@ struct Family {
 };
 
 // Allocation with an injectable failure hook (tests use it to check ENOMEM paths).
+// Stream-ordered (cudaMallocAsync / cudaFreeAsync) on the calling thread's
+// allocation stream, so that freeing never waits for the whole device.
 cudaError_t dev_alloc(void **p, size_t bytes);
 void dev_free(void *p);
+// Sets the calling thread's allocation stream for its lifetime (default: the
+// legacy stream).  Memory freed on a stream may be reused by later work of
+// that stream at once: free only what no other stream still uses.
+struct AllocStream {
+  explicit AllocStream(cudaStream_t st);
+  ~AllocStream();
+  cudaStream_t prev;
+};
 
 // ------------------------------------------------------------ LCS launch API
 enum OutMode : int {
@@ -88,6 +99,7 @@ enum OutMode : int {
   kOutRowsOrig = 1,  // int32 at rowoff(orig row) + orig col, only for orig col < orig row
   kOutRowbuf = 2,    // uint16 rowbuf[(row - row0) * ld + col], only for sorted col < sorted row
   kOutQuery = 3,     // int32 out[qrow * k + orig col]
+  kOutBatch = 4,     // uint16 out[row_base[entry] + sorted col], only for sorted col < sorted row
 };
 
 // A batch of pairs for the LCS kernels: a list of row sequences (with their
@@ -116,6 +128,9 @@ struct LcsBatch {
   int32_t row0 = 0;      // rowbuf: sorted id of its first row; rows mode: row_begin
   int32_t k = 0;         // family size (tri index)
   bool triangle = false; // restrict columns to sorted col < sorted row (by group bound)
+  // batched families: an explicit work list replaces the launch planner's grid
+  const int4 *items = nullptr;       // (first row entry, rows, first column group, unused)
+  const int64_t *row_base = nullptr; // kOutBatch: output offset of each row entry
 };
 
 // Enqueue the LCS kernels for a batch; returns a CUDA error code.  Adds the

@@ -49,6 +49,8 @@ cudaError_t launch_lcs(const LcsBatch &b, cudaStream_t st, int64_t *launches) {
   p.row0 = b.row0;
   p.k = b.k;
   p.triangle = b.triangle ? 1 : 0;
+  p.items = nullptr;
+  p.row_base = b.row_base;
   int32_t e0 = 0;
   while (e0 < b.n_rows) {
     const int w0 = b.h_row_w[e0];

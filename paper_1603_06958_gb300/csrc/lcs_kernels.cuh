@@ -40,6 +40,8 @@ struct KParams {
   int32_t row0;
   int32_t k;
   int triangle;
+  const int4 *items;        // batched families: one work item per CTA (else nullptr)
+  const int64_t *row_base;  // kOutBatch output offsets per row entry
 };
 
 constexpr int kTppThreads = 128;  // 4 warps = 4 column groups per CTA
@@ -78,6 +80,11 @@ __device__ __forceinline__ void emit_lcs(const KParams &p, int32_t e, int32_t ri
       static_cast<uint16_t *>(p.out)[(int64_t)(rid - p.row0) * p.ld + t] = (uint16_t)L;
       return;
     }
+    case kOutBatch: {
+      if (t >= rid) return;
+      static_cast<uint16_t *>(p.out)[p.row_base[e] + t] = (uint16_t)L;
+      return;
+    }
     default: {  // kOutQuery
       static_cast<int32_t *>(p.out)[(int64_t)rid * p.ld + p.col_perm[t]] = L;
       return;
@@ -89,28 +96,40 @@ __device__ __forceinline__ void emit_lcs(const KParams &p, int32_t e, int32_t ri
 // blockIdx.x: tile of R consecutive row entries; blockIdx.y: 128 consecutive
 // sorted columns (4 groups of 32).  Each thread owns one column and runs the
 // recurrence for all R rows of the tile at once (R independent carry chains).
+// With a work list (batched families), work item blockIdx.x names the tile
+// (at most R rows of one family) and its first column group instead.
 template <int W>
 __global__ void __launch_bounds__(kTppThreads) k_lcs_tpp(KParams p) {
   constexpr int R = TppRows<W>::R;
   extern __shared__ __align__(16) uint32_t sPeq[];  // R * W * 64 u32
-  const int32_t tile_e = p.e0 + (int32_t)blockIdx.x * R;
-  int32_t last_e = min(tile_e + R, p.e1) - 1;
+  int32_t tile_e, tile_end, gbase;
+  if (p.items) {
+    const int4 it = p.items[blockIdx.x];
+    tile_e = it.x;
+    tile_end = it.x + it.y;
+    gbase = it.z;
+  } else {
+    tile_e = p.e0 + (int32_t)blockIdx.x * R;
+    tile_end = min(tile_e + R, p.e1);
+    gbase = (int32_t)blockIdx.y * 4;
+  }
+  int32_t last_e = tile_end - 1;
   int32_t col_limit = p.triangle ? p.row_id[last_e] : p.n_cols;
-  if ((int32_t)blockIdx.y * kTppThreads >= col_limit) return;
+  if (gbase * kGroup >= col_limit) return;
 
   // stage the tile's Peq planes; rows shorter than W words are zero-padded
   for (int i = threadIdx.x; i < R * W * 16; i += kTppThreads) {
     int r = i / (W * 16), rem = i - r * (W * 16), w = rem >> 4;
     int32_t e = tile_e + r;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (e < p.e1 && w < (p.row_len[e] + 63) / 64)
+    if (e < tile_end && w < (p.row_len[e] + 63) / 64)
       v = reinterpret_cast<const uint4 *>(p.peq + (p.row_peq_off[e] + w) * kPeqWordU32)[rem & 15];
     reinterpret_cast<uint4 *>(sPeq)[i] = v;
   }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t g = (int32_t)blockIdx.y * 4 + warp;
+  const int32_t g = gbase + warp;
   if (g >= p.n_groups || g * kGroup >= col_limit) return;
 
   uint32_t V[R][2 * W];
@@ -153,7 +172,7 @@ __global__ void __launch_bounds__(kTppThreads) k_lcs_tpp(KParams p) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int32_t e = tile_e + r;
-    if (e >= p.e1) break;
+    if (e >= tile_end) break;
     int32_t L = 0;
 #pragma unroll
     for (int i = 0; i < 2 * W; ++i) L += __popc(~V[r][i]);
@@ -173,11 +192,18 @@ template <int NW>
 __global__ void __launch_bounds__(kWppThreads) k_lcs_wpp(KParams p) {
   constexpr int WP = 32 * NW;
   extern __shared__ __align__(16) uint64_t sP[];  // kCodes * WP
-  const int32_t e = p.e0 + (int32_t)blockIdx.x;
+  int32_t e, c_begin;
+  if (p.items) {
+    const int4 it = p.items[blockIdx.x];
+    e = it.x;
+    c_begin = it.z * kGroup;
+  } else {
+    e = p.e0 + (int32_t)blockIdx.x;
+    c_begin = (int32_t)blockIdx.y * kWppCols;
+  }
   const int32_t rid = p.row_id[e];
   const int32_t Wr = (p.row_len[e] + 63) / 64;
   const int32_t col_limit = p.triangle ? rid : p.n_cols;
-  const int32_t c_begin = (int32_t)blockIdx.y * kWppCols;
   if (c_begin >= col_limit) return;
   const int32_t c_end = min(c_begin + kWppCols, col_limit);
   const uint32_t *prow = p.peq + p.row_peq_off[e] * kPeqWordU32;

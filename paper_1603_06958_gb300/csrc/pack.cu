@@ -15,6 +15,10 @@
 namespace famsa {
 
 static std::atomic<int> g_alloc_fail_after{-1};
+static thread_local cudaStream_t tl_alloc_stream = nullptr;
+
+AllocStream::AllocStream(cudaStream_t st) : prev(tl_alloc_stream) { tl_alloc_stream = st; }
+AllocStream::~AllocStream() { tl_alloc_stream = prev; }
 
 cudaError_t dev_alloc(void **p, size_t bytes) {
   int n = g_alloc_fail_after.load();
@@ -23,10 +27,10 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
     g_alloc_fail_after.store(n - 1);
   }
   if (bytes == 0) bytes = 16;
-  return cudaMalloc(p, bytes);
+  return cudaMallocAsync(p, bytes, tl_alloc_stream);
 }
 void dev_free(void *p) {
-  if (p) cudaFree(p);
+  if (p) cudaFreeAsync(p, tl_alloc_stream);
 }
 
 int status_from_cuda(cudaError_t e) {
@@ -36,7 +40,6 @@ int status_from_cuda(cudaError_t e) {
 }
 
 // ----------------------------------------------------------------- kernels
-enum : int { kBadArg = 1, kTooLong = 2 };
 
 __global__ void k_lengths(const int64_t *off, int32_t k, int64_t base, int32_t *len,
                           int64_t *off0, int *status, int *max_len) {
@@ -160,6 +163,7 @@ __global__ void k_pack_peq(const uint8_t *res, const int64_t *off, const int32_t
   int lane = threadIdx.x & 31;
   if (s >= n) return;
   int32_t idx = map ? map[s] : s;
+  if (idx < 0) return;  // a pad slot of a batched family: no sequence, no Peq words
   const uint8_t *a = res + off[idx];
   int32_t len = (int32_t)(off[idx + 1] - off[idx]);
   int32_t W = (len + 63) / 64;
@@ -192,7 +196,7 @@ __global__ void k_col_layout(const uint8_t *res, const int64_t *off, const int32
     int32_t s = g * kGroup + lane;
     uint32_t w[4];
     int32_t len = s < k ? slen[s] : 0;
-    const uint8_t *a = s < k ? res + off[perm[s]] : res;
+    const uint8_t *a = len > 0 ? res + off[perm[s]] : res;  // pad slots have length 0
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint32_t v = 0;
@@ -230,6 +234,7 @@ int pack_family(const uint8_t *residues, const int64_t *offsets, int32_t k, bool
                 cudaStream_t st, Family **out) {
   *out = nullptr;
   cudaError_t err = cudaSuccess;
+  AllocStream alloc_on(st);
   Family *f = new Family();
   f->k = k;
   cudaGetDevice(&f->device);

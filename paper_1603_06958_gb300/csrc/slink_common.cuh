@@ -231,6 +231,20 @@ __device__ __forceinline__ int32_t merge_count(const uint64_t *key, int32_t sbas
 }
 
 // Buffers for the finalisation (all device, caller-owned)
+// Arguments of the cluster shared-memory row update: insert points r0..r1-1,
+// whose similarity rows are rowbuf[(n - r0) * ld ..].
+struct SmemArgs {
+  SlinkState s;
+  const uint16_t *rowbuf;
+  int64_t ld;  // even, so every row starts on a 4-byte boundary
+  int32_t r0, r1;
+  int32_t P;   // positions per CTA
+  // batched families: cluster c takes batch[c] (its own state, rows and sizes)
+  const SmemArgs *batch;
+};
+cudaError_t launch_slink_smem_batch(const SmemArgs *d_args, int32_t n_clusters, int cl, int32_t Pmax,
+                                    bool narrow, cudaStream_t st);
+
 struct FinBufs {
   int32_t *idx, *posof, *it, *rt, *pi, *sub_lo, *sub_hi, *ordA, *ordB, *rank, *sorder, *merges,
       *sizes;

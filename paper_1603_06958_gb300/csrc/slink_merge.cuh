@@ -16,7 +16,7 @@ namespace famsa {
 // every element starts as its own run.  Threads own positions [cb, ce).
 // Returns the buffer index holding the merged order.
 template <class K = KeysWide>
-__device__ __forceinline__ int merge_rounds(SlinkState &S, cg::cluster_group &cluster, int32_t m,
+__device__ __forceinline__ int merge_rounds(const SlinkState &S, cg::cluster_group &cluster, int32_t m,
                                             int32_t x0, bool natural, const int32_t *sRunsA,
                                             int32_t nA, const int32_t *sRunsB, int32_t nB,
                                             int32_t cb, int32_t ce, bool count_rounds) {

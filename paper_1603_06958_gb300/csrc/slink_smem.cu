@@ -23,14 +23,6 @@
 
 namespace famsa {
 
-struct SmemArgs {
-  SlinkState s;
-  const uint16_t *rowbuf;
-  int64_t ld;  // even, so every row starts on a 4-byte boundary
-  int32_t r0, r1;
-  int32_t P;   // positions per CTA
-};
-
 constexpr int kSmemThreads = 512;
 constexpr size_t kSmemBytesPerPos = 6 * sizeof(uint64_t) + 9 * sizeof(int32_t);
 constexpr int kLocalRuns = 16;     // run starts a CTA may hold per side (fast merge)
@@ -61,9 +53,13 @@ __device__ __forceinline__ uint32_t half_of(int32_t word, int32_t node) {
 }
 
 template <class K>
-__global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs a) {
+__global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
   cg::cluster_group cluster = cg::this_cluster();
   const int32_t ncta = (int32_t)cluster.num_blocks();
+  __shared__ SmemArgs sArgs;
+  if (threadIdx.x == 0) sArgs = arg.batch ? arg.batch[blockIdx.x / ncta] : arg;
+  __syncthreads();
+  const SmemArgs &a = sArgs;
   const int32_t cta = (int32_t)cluster.block_rank();
   const int32_t P = a.P;
   const int32_t base = cta * P;
@@ -72,7 +68,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs a) {
   const int32_t i0 = threadIdx.x * E;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   const int32_t tid = cta * T + threadIdx.x;
-  SlinkState &S = a.s;
+  const SlinkState &S = a.s;
   uint64_t *ctl = S.ctl;
   constexpr uint64_t INF = K::kInf;
 
@@ -699,7 +695,7 @@ int smem_cluster_for(int32_t k, int force) {
 }
 
 template <class K>
-static cudaError_t launch_smem_t(const SmemArgs &args, int cl, cudaStream_t st) {
+static cudaError_t launch_smem_t(const SmemArgs &args, int cl, cudaStream_t st, int32_t n_clusters) {
   const size_t dyn = smem_bytes_for(args.P);
   cudaError_t e = cudaFuncSetAttribute(k_slink_smem<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
@@ -708,7 +704,7 @@ static cudaError_t launch_smem_t(const SmemArgs &args, int cl, cudaStream_t st) 
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cl, 1, 1);
+  cfg.gridDim = dim3((unsigned)(cl * n_clusters), 1, 1);
   cfg.blockDim = dim3(g_smem_threads, 1, 1);
   cfg.dynamicSmemBytes = dyn;
   cfg.stream = st;
@@ -731,7 +727,18 @@ cudaError_t launch_slink_smem(const SlinkState &S, const uint16_t *rowbuf, int64
   args.r0 = r0;
   args.r1 = r1;
   args.P = (k + cl - 1) / cl;
-  return narrow ? launch_smem_t<KeysNarrow>(args, cl, st) : launch_smem_t<KeysWide>(args, cl, st);
+  args.batch = nullptr;
+  return narrow ? launch_smem_t<KeysNarrow>(args, cl, st, 1) : launch_smem_t<KeysWide>(args, cl, st, 1);
+}
+
+cudaError_t launch_slink_smem_batch(const SmemArgs *d_args, int32_t n_clusters, int cl, int32_t Pmax,
+                                    bool narrow, cudaStream_t st) {
+  if (n_clusters <= 0) return cudaSuccess;
+  SmemArgs args = {};
+  args.P = Pmax;  // sizes the dynamic shared memory of every cluster
+  args.batch = d_args;
+  return narrow ? launch_smem_t<KeysNarrow>(args, cl, st, n_clusters)
+                : launch_smem_t<KeysWide>(args, cl, st, n_clusters);
 }
 
 // narrow keys (num << 32 | den) -> wide keys (num << 16 | den), in place

@@ -1,0 +1,124 @@
+"""Batched families: famsa_batch_tree must give, for every family, exactly the
+tree famsa_slink_tree gives for that family alone, and the oracle's tree for
+the small ones -- on a mix that covers one-point and two-point families,
+tie-heavy small alphabets, duplicates, long sequences (warp-per-pair LCS),
+several row-update cluster sizes and a family too large for one cluster's
+shared memory (global-memory row update), and on repeated graph launches.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fg():
+    from paper_1603_06958_gb300 import build
+    build.build()
+    import paper_1603_06958_gb300 as m
+    m.load()
+    return m
+
+
+def concat(fams):
+    res = np.concatenate([r for r, _ in fams])
+    offs, fo, base = [np.zeros(1, np.int64)], [0], 0
+    for r, o in fams:
+        offs.append(o[1:] + base)
+        base += int(o[-1])
+        fo.append(fo[-1] + len(o) - 1)
+    return res, np.concatenate(offs), np.array(fo, np.int64)
+
+
+KEYS = ("pi", "lambda_num", "lambda_den", "merges", "h_num", "h_den", "sizes")
+
+
+def assert_same(got, want, tag):
+    for key in KEYS:
+        g, w = np.asarray(got[key]), np.asarray(want[key])
+        assert np.array_equal(g.reshape(w.shape), w), (tag, key)
+
+
+def alone(fg, r, o):
+    fam = fg.pack_peq(r, o)
+    t = fg.slink_tree(fam)
+    fam.free()
+    return t
+
+
+SMALL = [
+    dict(k=1, seed=1, root_len=40),
+    dict(k=2, seed=2, root_len=30),
+    dict(k=3, seed=3, root_len=5, alphabet=2),
+    dict(k=33, seed=4, root_len=20, alphabet=3, dup_frac=0.2),
+    dict(k=64, seed=5, root_len=120),
+    dict(k=150, seed=6, root_len=60, alphabet=4, sub_rate=0.1),
+    dict(k=97, seed=7, root_len=2300, indel_rate=0.002),  # 36+ words: warp-per-pair rows
+    dict(k=250, seed=8, root_len=300, ext_frac=0.3),
+]
+
+
+def test_batch_small_families_match_oracle_and_alone(fg):
+    fams = []
+    for c in SMALL:
+        c = dict(c)
+        fams.append(synth.family(c.pop("k"), c.pop("seed"), **c))
+    res, off, fo = concat(fams)
+    b = fg.batch_pack(res, off, fo)
+    out = fg.batch_tree(b)
+    st = b.stats()
+    assert st["pairs"] == sum((len(o) - 1) * (len(o) - 2) // 2 for _, o in fams)
+    assert st["lcs_items"] > 0 and st["lcs_ns"] > 0
+    for f, (r, o) in enumerate(fams):
+        got = fg.batch_family_tree(out, b, f)
+        assert_same(got, oracle.tree(r, o), ("oracle", f))
+        assert_same(got, alone(fg, r, o), ("alone", f))
+    # the graph runs again with the same result
+    out2 = fg.batch_tree(b)
+    for key in KEYS:
+        assert np.array_equal(np.asarray(out[key]), np.asarray(out2[key])), key
+    b.free()
+
+
+def test_batch_cluster_sizes_and_global_path(fg):
+    # k around 2,600 and 5,000 take 2- and 4-CTA clusters; k = 36,000 exceeds one
+    # cluster's shared memory and runs the global-memory row update
+    fams = [synth.family(2600, 11, root_len=60, alphabet=4),
+            synth.family(40, 12, root_len=80),
+            synth.family(5000, 13, root_len=40, alphabet=5),
+            synth.family(36000, 14, root_len=12, alphabet=4, sub_rate=0.1)]
+    res, off, fo = concat(fams)
+    b = fg.batch_pack(res, off, fo)
+    out = fg.batch_tree(b)
+    assert b.stats()["global_update_families"] == 1
+    for f, (r, o) in enumerate(fams):
+        assert_same(fg.batch_family_tree(out, b, f), alone(fg, r, o), ("alone", f))
+    b.free()
+
+
+def test_batch_device_inputs_and_outputs(fg):
+    import torch
+    fams = [synth.family(k, 20 + k, root_len=70) for k in (5, 120, 31, 32, 33)]
+    res, off, fo = concat(fams)
+    b = fg.batch_pack(torch.from_numpy(res).cuda(), torch.from_numpy(off).cuda(), fo)
+    out = fg.batch_tree(b, device=True)
+    torch.cuda.synchronize()
+    host = {k: v.cpu().numpy() for k, v in out.items()}
+    for f, (r, o) in enumerate(fams):
+        assert_same(fg.batch_family_tree(host, b, f), oracle.tree(r, o), ("oracle", f))
+    b.free()
+
+
+def test_batch_argument_errors(fg):
+    r, o = synth.family(10, 1, root_len=20)
+    with pytest.raises(fg.FamsaError):
+        fg.batch_pack(r, o, np.array([0, 4, 4, 10]))      # an empty family
+    with pytest.raises(fg.FamsaError):
+        fg.batch_pack(r, o, np.array([0, 4, 9]))          # does not end at n_seqs
+    bad = r.copy()
+    bad[3] = 25
+    with pytest.raises(fg.FamsaError):
+        fg.batch_pack(bad, o, np.array([0, 5, 10]))       # residue code out of range
