@@ -49,6 +49,9 @@ WORKLOADS = {
     "plain1k": "plain family: k=1,000, root length 250, clip 50-400, seed 1",
     "scale400k": "scale family: k=400,000, root length log-normal (median 250, sigma 0.5) "
                  "clamped 30-3,000, 1% X/B/Z ambiguity residues, 25-letter alphabet, seed 1",
+    "serve": "serving: seeded Poisson stream of 120 requests, 70% new families (k log-uniform "
+             "100-50,000, plain20k length model) and 30% batches of 1-256 query sequences "
+             "scored against a resident family; admission by an HBM budget (64 GB), 8 slots",
     "batch512": "batched: 512 independent families, k log-uniform 50-5,000, root length "
                 "log-uniform 30-2,000, 0.02 subs/site and 0.01 indels/site per branch, seed 1; "
                 "one famsa_batch_pack + famsa_batch_tree (one CUDA graph) per step",
@@ -63,6 +66,9 @@ def make_family(workload: str, seed: int, k: int | None):
         return synth.plain1k(seed)
     if workload == "scale400k":
         return synth.scale400k(seed, **({"k": k} if k else {}))
+    if workload == "serve":  # the largest family of the stream stands for it
+        fams = [(r[1], r[2]) for r in serve_requests(seed) if r[0] == "tree"]
+        return max(fams, key=lambda t: cells_and_pairs(t[1])[0])
     if workload == "batch512":  # one family stands for the batch (the oracle arm samples its rows)
         fams = synth.batch512(seed)
         return max(fams, key=lambda t: cells_and_pairs(t[1])[0])
@@ -395,6 +401,109 @@ def cpu_baseline_families(fams, budget_s=15.0):
                       % (n, done_cells, t_used)}
 
 
+def serve_requests(seed: int, n: int = 120):
+    """The seeded request stream: (kind, family index or arrays, arrival gap in
+    units of the mean gap)."""
+    import synth
+    rng = np.random.default_rng(seed)
+    reqs, n_trees = [], 0
+    for i in range(n):
+        gap = float(rng.exponential(1.0))
+        if i == 0 or rng.random() < 0.7 or n_trees == 0:
+            k = int(np.exp(rng.uniform(np.log(100), np.log(50000))))
+            res, off = synth.plain20k(seed * 100003 + i, k=k)
+            reqs.append(("tree", res, off, gap))
+            n_trees += 1
+        else:
+            nq = int(rng.integers(1, 257))
+            q, qo = synth.plain20k(seed * 100003 + i, k=nq)
+            target = int(rng.integers(0, n_trees))  # the target-th tree request so far
+            reqs.append(("query", q, qo, gap, target))
+    return reqs
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving: the request stream through famsa_server_* -- serially (one slot,
+    all submitted at once: plain launches one after another), as a burst with 8
+    slots (capacity), and as Poisson arrivals at 75% of that capacity (latency)."""
+    import torch
+    import paper_1603_06958_gb300 as fg
+
+    torch.cuda.set_device(local_rank)
+    fg.load()
+    reqs = serve_requests(args.seed + rank)
+    budget = 64 << 30
+
+    def run(slots, rate=None):
+        srv = fg.Server(budget, slots)
+        ids, trees = [], []
+        t0 = time.perf_counter()
+        clk_next = t0
+        for r in reqs:
+            if rate is not None:
+                clk_next += r[3] / rate
+                d = clk_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+            if r[0] == "tree":
+                rid = srv.submit_tree(r[1], r[2], keep=True)
+                trees.append(rid)
+            else:
+                rid = srv.submit_query(trees[r[4]], r[1], r[2])
+            ids.append(rid)
+        for rid in ids:
+            rc = srv.wait(rid)
+            if rc != fg.FAMSA_OK:
+                raise RuntimeError("request %d failed: %s" % (rid, fg.strerror(rc)))
+        makespan = time.perf_counter() - t0
+        infos = [srv.info(i) for i in ids]
+        st = srv.stats()
+        srv.close()
+        return makespan, infos, st
+
+    run(8)  # warm-up: kernels loaded, memory pools grown
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_serial, inf_serial, _ = run(1)
+    t_burst, inf_burst, st_burst = run(8)
+    rate = 0.75 * len(reqs) / t_burst
+    t_pois, inf_pois, st_pois = run(8, rate)
+    clk = clocks.stop()
+    cells = float(sum(i["cells"] for i in inf_burst))
+
+    def lat(infos, kind=None):
+        v = np.array([i["latency_ns"] for i in infos if kind is None or i["kind"] == kind]) / 1e6
+        return {"p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99)),
+                "mean_ms": float(v.mean()), "n": int(len(v))}
+
+    n_tree = sum(1 for r in reqs if r[0] == "tree")
+    line = {
+        "metric": METRIC, "value": cells / t_burst / 1e9, "unit": "GCUPS", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_burst, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["serve"], "requests": len(reqs), "tree_requests": n_tree,
+                   "query_requests": len(reqs) - n_tree, "cells": cells,
+                   "serial_one_slot_s": t_serial, "serial_gcups": cells / t_serial / 1e9,
+                   "burst_8_slots_s": t_burst, "speedup_vs_serial": t_serial / t_burst,
+                   "peak_running": st_burst["peak_running"],
+                   "peak_reserved_gb": st_burst["peak_reserved"] / 2 ** 30,
+                   "poisson_rate_per_s": rate, "poisson_makespan_s": t_pois,
+                   "poisson_gcups": cells / t_pois / 1e9,
+                   "latency_poisson": {"all": lat(inf_pois), "tree": lat(inf_pois, 0),
+                                       "query": lat(inf_pois, 1)},
+                   "latency_burst": lat(inf_burst), "latency_serial": lat(inf_serial),
+                   "inputs": "host buffers copied at submission; results copied back to the host",
+                   "l2": "inputs larger than L2 across the stream"},
+        "roofline": None,
+        "e2e": {"value": cells / t_burst / 1e9, "unit": "GCUPS",
+                "h2d_bytes_per_step": int(sum(r[1].nbytes + r[2].nbytes for r in reqs)),
+                "d2h_bytes_per_step": 0},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1603_06958_gb300 as fg
@@ -581,7 +690,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    rc = (run_batch if args.workload == "batch512" else run_ours)(args, rank, world, local_rank)
+    arm = {"batch512": run_batch, "serve": run_serve}.get(args.workload, run_ours)
+    rc = arm(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

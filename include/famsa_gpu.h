@@ -243,6 +243,62 @@ int famsa_batch_stats(const famsa_batch *b, int64_t *stats);
 /* Release a batch and its device memory (NULL is ignored). */
 void famsa_batch_free(famsa_batch *b);
 
+/*
+ * Serving loop -- guide-tree requests for new families and query batches
+ * scored against resident families, run by a request queue with admission
+ * by an HBM budget and continuous batching: each of `slots` worker threads
+ * owns a CUDA stream and takes the first queued request that fits the free
+ * part of the budget (a query also needs its family resident); requests
+ * that arrive while others run start as soon as a slot and memory free up,
+ * and their kernels overlap on the device.  A request that is older than
+ * about one second is not overtaken.  A request larger than the whole
+ * budget runs when nothing else does.  Each result equals the
+ * single-request call (famsa_slink_tree / famsa_lcs_query) on the same
+ * input, whatever runs beside it.  All inputs and outputs are host buffers;
+ * inputs are copied at submission.  The calls below are thread-safe.
+ *
+ * famsa_server_create: budget in bytes of device memory for running and
+ *   resident requests (estimated per request), slots in 1..64.  Uses the
+ *   current device.
+ * famsa_server_submit_tree: a family (see the conventions); keep_resident
+ *   keeps its packed tables on the device for queries until released.
+ * famsa_server_submit_query: nq queries against the family of an earlier
+ *   tree request submitted with keep_resident (it may still be running).
+ *   A query whose family fails ends with EINVAL.
+ * famsa_server_wait: wait up to timeout_ms (< 0: forever) for a request;
+ *   returns its status (FAMSA_OK or the error of its library call), or
+ *   ETIMEOUT if it is still queued or running, EINVAL for an unknown id.
+ * famsa_server_tree_result / famsa_server_query_result: copy a finished
+ *   request's results, laid out as famsa_slink_tree / famsa_lcs_query give
+ *   them (any tree output may be NULL).  EINVAL unless finished with OK.
+ * famsa_server_request_info: info[7] int64 = status, kind (0 tree, 1 query),
+ *   sequences (k or nq), ns from submission to start (-1 while queued), ns
+ *   from submission to completion (-1 before), LCS cells, bytes reserved.
+ * famsa_server_release: forget a request and free a resident family (after
+ *   its running queries end).
+ * famsa_server_stats: stats[8] int64 = submitted, done, failed, queued,
+ *   running, most running at once, bytes reserved now, most reserved.
+ * famsa_server_destroy: fails queued requests, waits for running ones,
+ *   frees everything.
+ * Errors: EINVAL (bad argument or id), EBUSY (more than 2^20 queued).
+ * The paper has no serving loop; this is the library's own scheduler.
+ */
+typedef struct famsa_server famsa_server;
+int famsa_server_create(int64_t hbm_budget_bytes, int32_t slots, famsa_server **out);
+int famsa_server_submit_tree(famsa_server *s, const uint8_t *residues, const int64_t *offsets,
+                             int32_t k, int keep_resident, int64_t *request_id);
+int famsa_server_submit_query(famsa_server *s, int64_t family_request, const uint8_t *q,
+                              const int64_t *q_offsets, int32_t nq, int64_t *request_id);
+int famsa_server_wait(famsa_server *s, int64_t request_id, int64_t timeout_ms);
+int famsa_server_tree_result(famsa_server *s, int64_t request_id, int32_t *pi, uint64_t *lambda_num,
+                             uint32_t *lambda_den, int32_t *merges, uint64_t *h_num, uint32_t *h_den,
+                             int32_t *sizes);
+int famsa_server_query_result(famsa_server *s, int64_t request_id, int32_t *out);
+int famsa_server_request_info(famsa_server *s, int64_t request_id, int64_t *info);
+int famsa_server_release(famsa_server *s, int64_t request_id);
+int famsa_server_stats(famsa_server *s, int64_t *stats);
+void famsa_server_destroy(famsa_server *s);
+
 /* Release a handle and its device memory (NULL is ignored).  Waits for the
  * handle's pending work. */
 void famsa_free(famsa_family *f);

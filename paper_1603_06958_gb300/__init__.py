@@ -77,6 +77,18 @@ def load(path: str = LIB_PATH):
             "famsa_batch_tree": ([_P, _P, u64p, _P, _P, u64p, _P, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_batch_stats": ([_P, _P], ctypes.c_int),
             "famsa_batch_free": ([_P], None),
+            "famsa_server_create": ([ctypes.c_int64, i32, ctypes.POINTER(_P)], ctypes.c_int),
+            "famsa_server_submit_tree": ([_P, _P, _P, i32, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
+                                         ctypes.c_int),
+            "famsa_server_submit_query": ([_P, ctypes.c_int64, _P, _P, i32,
+                                           ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+            "famsa_server_wait": ([_P, ctypes.c_int64, ctypes.c_int64], ctypes.c_int),
+            "famsa_server_tree_result": ([_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+            "famsa_server_query_result": ([_P, ctypes.c_int64, _P], ctypes.c_int),
+            "famsa_server_request_info": ([_P, ctypes.c_int64, _P], ctypes.c_int),
+            "famsa_server_release": ([_P, ctypes.c_int64], ctypes.c_int),
+            "famsa_server_stats": ([_P, _P], ctypes.c_int),
+            "famsa_server_destroy": ([_P], None),
             "famsa_free": ([_P], None),
             "famsa_last_stats": ([_P, _P], ctypes.c_int),
             "famsa_debug_fail_alloc_after": ([ctypes.c_int], ctypes.c_int),
@@ -317,6 +329,88 @@ def famsa_batch_tree(b: Batch, device: bool = False, stream=None) -> dict:
 
 
 batch_tree = famsa_batch_tree
+
+
+class Server:
+    """The library's serving loop (see famsa_server_* in the C header): host
+    inputs and outputs, admission by an HBM budget, `slots` concurrent requests."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int):
+        h = _P()
+        _check(load().famsa_server_create(int(hbm_budget_bytes), int(slots), ctypes.byref(h)),
+               "famsa_server_create")
+        self.handle = h.value
+        self.sizes = {}
+
+    def submit_tree(self, residues, offsets, keep: bool = False) -> int:
+        r = np.ascontiguousarray(residues, dtype=np.uint8)
+        o = np.ascontiguousarray(offsets, dtype=np.int64)
+        rid = ctypes.c_int64()
+        _check(load().famsa_server_submit_tree(self.handle, r.ctypes.data, o.ctypes.data, len(o) - 1,
+                                               int(keep), ctypes.byref(rid)), "famsa_server_submit_tree")
+        self.sizes[rid.value] = ("tree", len(o) - 1, None)
+        return rid.value
+
+    def submit_query(self, family_request: int, q, q_offsets) -> int:
+        r = np.ascontiguousarray(q, dtype=np.uint8)
+        o = np.ascontiguousarray(q_offsets, dtype=np.int64)
+        rid = ctypes.c_int64()
+        _check(load().famsa_server_submit_query(self.handle, int(family_request), r.ctypes.data,
+                                                o.ctypes.data, len(o) - 1, ctypes.byref(rid)),
+               "famsa_server_submit_query")
+        self.sizes[rid.value] = ("query", len(o) - 1, self.sizes[family_request][1])
+        return rid.value
+
+    def wait(self, request_id: int, timeout_ms: int = -1) -> int:
+        return load().famsa_server_wait(self.handle, int(request_id), int(timeout_ms))
+
+    def tree_result(self, request_id: int) -> dict:
+        k = self.sizes[request_id][1]
+        m = max(k - 1, 0)
+        out = {"pi": np.empty(k, np.int32), "lambda_num": np.empty(k, np.uint64),
+               "lambda_den": np.empty(k, np.uint32), "merges": np.empty(2 * m, np.int32),
+               "h_num": np.empty(m, np.uint64), "h_den": np.empty(m, np.uint32),
+               "sizes": np.empty(m, np.int32)}
+        ptrs = [out[n].ctypes.data for n in ("pi", "lambda_num", "lambda_den", "merges", "h_num",
+                                             "h_den", "sizes")]
+        _check(load().famsa_server_tree_result(self.handle, int(request_id), *ptrs),
+               "famsa_server_tree_result")
+        out["merges"] = out["merges"].reshape(m, 2)
+        return out
+
+    def query_result(self, request_id: int) -> np.ndarray:
+        _, nq, k = self.sizes[request_id]
+        out = np.empty(nq * k, np.int32)
+        _check(load().famsa_server_query_result(self.handle, int(request_id), out.ctypes.data),
+               "famsa_server_query_result")
+        return out.reshape(nq, k)
+
+    def info(self, request_id: int) -> dict:
+        a = np.zeros(7, np.int64)
+        _check(load().famsa_server_request_info(self.handle, int(request_id), a.ctypes.data),
+               "famsa_server_request_info")
+        return dict(zip(["status", "kind", "n", "queue_ns", "latency_ns", "cells", "reserved"],
+                        [int(x) for x in a]))
+
+    def release(self, request_id: int):
+        _check(load().famsa_server_release(self.handle, int(request_id)), "famsa_server_release")
+
+    def stats(self) -> dict:
+        a = np.zeros(8, np.int64)
+        _check(load().famsa_server_stats(self.handle, a.ctypes.data), "famsa_server_stats")
+        return dict(zip(["submitted", "done", "failed", "queued", "running", "peak_running",
+                         "reserved", "peak_reserved"], [int(x) for x in a]))
+
+    def close(self):
+        if self.handle:
+            load().famsa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def batch_family_tree(out: dict, b: Batch, f: int) -> dict:

@@ -19,6 +19,8 @@
 // local capacity fall back to pairwise merges in global memory.  Keys are
 // compared by cross multiplication: packed as (indel^2 << 32) | LCS when every
 // length is at most 32767, else (indel^2 << 16) | LCS.
+#include <mutex>
+
 #include "slink_merge.cuh"
 
 namespace famsa {
@@ -694,15 +696,34 @@ int smem_cluster_for(int32_t k, int force) {
   return 0;
 }
 
+// The kernel's dynamic shared-memory cap and non-portable cluster permission
+// are set once, to the device maxima: a per-launch value could be lowered by
+// a concurrent caller between its setting and another caller's launch.
+template <class K>
+static cudaError_t smem_kernel_attributes() {
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] {
+    int device = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slink_smem<K>);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_slink_smem<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_slink_smem<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    result = e;
+  });
+  return result;
+}
+
 template <class K>
 static cudaError_t launch_smem_t(const SmemArgs &args, int cl, cudaStream_t st, int32_t n_clusters) {
   const size_t dyn = smem_bytes_for(args.P);
-  cudaError_t e = cudaFuncSetAttribute(k_slink_smem<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  cudaError_t e = smem_kernel_attributes<K>();
   if (e != cudaSuccess) return e;
-  if (cl > 8) {
-    e = cudaFuncSetAttribute(k_slink_smem<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(cl * n_clusters), 1, 1);
   cfg.blockDim = dim3(g_smem_threads, 1, 1);
