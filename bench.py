@@ -261,8 +261,13 @@ def run_batch(args, rank, world, local_rank):
         t = fg.batch_tree(b, device=True)
         return b, t
 
+    tune = None
     for _ in range(args.warmup):
         b, _ = step()
+        s0 = b.stats()
+        if tune is None:  # the first plan of the process runs the autotuner
+            tune = {"widths_timed": s0["tuned_widths"], "seconds": s0["tune_ns"] / 1e9,
+                    "rows_per_tile": {w: fg.debug_tpp_rows(w) for w in range(1, 33)}}
         b.free()
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
@@ -361,7 +366,8 @@ def run_batch(args, rank, world, local_rank):
                    "plain_ms": plain_ms,
                    "plain_gcups": (cells / (plain_ms * 1e-3) / 1e9) if plain_ms else None,
                    "speedup_vs_plain": (plain_ms / ms_step) if plain_ms else None,
-                   "lcs_items": st["lcs_items"], "lcs_widths": st["lcs_widths"]},
+                   "lcs_items": st["lcs_items"], "lcs_widths": st["lcs_widths"],
+                   "autotuner": tune},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_lcs_tpp / k_lcs_wpp over the batch work lists",
@@ -513,6 +519,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     fg.load()
+    fg.debug_set_update_path(args.update_path)
+    fg.debug_set_global_variant(args.global_variant)
     res, off = make_family(args.workload, args.seed + rank, args.k)
     k = len(off) - 1
     cells, pairs = cells_and_pairs(off)
@@ -671,6 +679,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=int, default=12)
+    ap.add_argument("--update-path", type=int, default=0, choices=[0, 1, 2],
+                    help="row-update kernel: 0 automatic, 1 cluster shared memory, 2 global memory "
+                         "(profiling; the default picks by family size)")
+    ap.add_argument("--global-variant", type=int, default=0, choices=[0, 1],
+                    help="global-memory row update: 0 = 1,024 threads a CTA, 1 = 512")
     ap.add_argument("--no-plain", action="store_true",
                     help="batch512: skip timing the one-family-at-a-time comparator")
     ap.add_argument("--int-peaks", action="store_true",

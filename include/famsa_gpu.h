@@ -237,7 +237,14 @@ int famsa_batch_tree(famsa_batch *b, int32_t *pi, uint64_t *lambda_num, uint32_t
  * 4 kernel launches captured in the graph, 5 LCS kernel widths, 6 families
  * on the global-memory row update, 7..9 device time in ns of the LCS, the
  * row update and the finalisation in the last graph launch (this call waits
- * for that launch), 10..11 reserved.  Zero before the first tree. */
+ * for that launch), 10 kernel widths the autotuner timed for this plan, 11
+ * ns the autotuner took.  Zero before the first tree.
+ *
+ * The autotuner: the first plan with at least 64 rows of a thread-per-pair
+ * width times each allowed rows-per-tile choice (1, 2 or 4 rows, with rows
+ * x words <= 32) on the same 1,024-row sample and keeps the fastest for the
+ * process, for batches and single families alike; results do not depend on
+ * the choice. */
 int famsa_batch_stats(const famsa_batch *b, int64_t *stats);
 
 /* Release a batch and its device memory (NULL is ignored). */

@@ -50,10 +50,28 @@ int famsa_debug_set_update_threads(int threads);
  * (no overlap of the two streams), for timing studies; 0: overlap (default). */
 int famsa_debug_set_serial(int on);
 
-/* Kilocycles spent by one thread of the shared-memory row-update kernel in
- * the sub-steps of its last tree build on f (out16: 16 int64; 0..7 the
- * common path, 8..13 the run merge in shared memory). */
+/* Kilocycles spent by one thread of the row-update kernel in the sub-steps
+ * of its last tree build on f (out16: 16 int64).  Shared-memory kernel: 0..7
+ * the common path, 8..13 the run merge in shared memory.  Global-memory
+ * kernel: 0 phase-A tiles, 1..3 warp totals and the cluster barrier, 4 CTA
+ * prefixes, 5 forward scan, 6 backward scan and pointer update, 7..8 first
+ * minimum and the barrier, 9 re-layout, 10 its barrier, 11 run merges. */
 int famsa_debug_sub_kcycles(const famsa_family *f, int64_t *out16);
+
+/* Rows per tile r (1, 2 or 4 with r * w <= 32; 0 = the default) of the
+ * thread-per-pair LCS kernel for rows of w 64-bit words, as the batch
+ * autotuner sets it.  Results are identical for every r.  EINVAL for other
+ * values.  famsa_debug_tpp_rows returns the r in use for w (-1 for a bad w). */
+int famsa_debug_set_tpp_rows(int w, int r);
+int famsa_debug_tpp_rows(int w);
+
+/* Batch autotuner on (1, default) or off (0; also forgets the widths tuned
+ * so far, but keeps their choices until famsa_debug_set_tpp_rows resets them). */
+int famsa_debug_set_autotune(int on);
+
+/* Threads a CTA of the global-memory row-update kernel: 0 (default) 1,024,
+ * 1 512.  Results are identical.  EINVAL outside 0..1. */
+int famsa_debug_set_global_variant(int v);
 
 /* Thread-instructions per second of one integer instruction kind run as
  * many independent chains over the whole device (kind 0 LOP3, 1 IADD3,

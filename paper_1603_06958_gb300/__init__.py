@@ -99,6 +99,10 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
             "famsa_debug_int_pipe_rate": ([ctypes.c_int, _P], ctypes.c_int),
+            "famsa_debug_set_global_variant": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_tpp_rows": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "famsa_debug_tpp_rows": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_autotune": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_insertion_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -286,7 +290,8 @@ class Batch:
         s = np.zeros(12, dtype=np.int64)
         _check(load().famsa_batch_stats(self.handle, s.ctypes.data), "famsa_batch_stats")
         keys = ["cells", "word_steps", "pairs", "lcs_items", "graph_launches", "lcs_widths",
-                "global_update_families", "lcs_ns", "update_ns", "finalize_ns"]
+                "global_update_families", "lcs_ns", "update_ns", "finalize_ns", "tuned_widths",
+                "tune_ns"]
         return {k: int(v) for k, v in zip(keys, s)}
 
 
@@ -515,6 +520,24 @@ def debug_int_pipe_rate(kind: int) -> float:
     out = ctypes.c_double()
     _check(load().famsa_debug_int_pipe_rate(kind, ctypes.byref(out)), "famsa_debug_int_pipe_rate")
     return out.value
+
+
+def debug_set_tpp_rows(w: int, r: int):
+    """Rows per thread-per-pair tile for width w (0 = default)."""
+    _check(load().famsa_debug_set_tpp_rows(int(w), int(r)), "famsa_debug_set_tpp_rows")
+
+
+def debug_tpp_rows(w: int) -> int:
+    return int(load().famsa_debug_tpp_rows(int(w)))
+
+
+def debug_set_autotune(on: bool):
+    _check(load().famsa_debug_set_autotune(int(on)), "famsa_debug_set_autotune")
+
+
+def debug_set_global_variant(v: int):
+    """Global-memory row update: 0 = 1,024 threads a CTA, 1 = 512."""
+    _check(load().famsa_debug_set_global_variant(int(v)), "famsa_debug_set_global_variant")
 
 
 def debug_set_cluster(ctas: int):

@@ -15,7 +15,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfamsa_gpu.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu",
+SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu", "lcs_tpp_d.cu",
            "lcs_wpp.cu", "slink.cu", "slink_global.cu", "slink_smem.cu", "finalize.cu",
            "noalloc.cu", "int_peak.cu", "batch.cu", "server.cu"]
 HEADERS = ["famsa_internal.cuh", "lcs_kernels.cuh", "lcs_step.inc", "slink_common.cuh",

@@ -13,6 +13,8 @@
 // cluster size in one launch.  The finalisation gives each family's pointer
 // representation and merge list in that family's own labels.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <mutex>
 #include <vector>
 
@@ -329,7 +331,6 @@ static cudaError_t upload_vec(Arena &A, const std::vector<T> &v, T **d, cudaStre
   return cudaMemcpyAsync(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
 }
 
-static int tpp_R(int W) { return W <= 4 ? 4 : (W <= 8 ? 2 : 1); }
 static int wpp_NW(int W) {
   int nw = 1;
   while (32 * nw < W) nw *= 2;
@@ -338,13 +339,155 @@ static int wpp_NW(int W) {
 
 struct Bucket {
   bool wpp;
-  int kw;  // W (thread-per-pair) or NW (warp-per-pair)
+  int kw;     // W (thread-per-pair) or NW (warp-per-pair)
+  int R = 1;  // rows per tile
   std::vector<int4> items;
 };
+
+struct BRow {
+  int32_t rid;
+  int32_t f;
+};
+
+// Row entries (Peq offset, length, sorted id, output base) and work items of
+// a list of rows, tiles of at most R rows of one family.
+struct RowArrays {
+  std::vector<int64_t> peq, base;
+  std::vector<int32_t> len, id;
+};
+
+static void append_rows(const Batch *b, const std::vector<BRow> &rows, size_t count, bool wpp, int R,
+                        const std::vector<int64_t> &h_peq_off, const std::vector<int64_t> &rb_off,
+                        const std::vector<int64_t> &ld, RowArrays &ra, std::vector<int4> &items) {
+  size_t i = 0;
+  while (i < count) {
+    const int32_t f = rows[i].f;
+    size_t j = i + 1;
+    while (j < count && j - i < (size_t)R && rows[j].f == f) ++j;
+    const int32_t e0 = (int32_t)ra.id.size();
+    for (size_t q = i; q < j; ++q) {
+      const int32_t rid = rows[q].rid;
+      ra.peq.push_back(h_peq_off[rid]);
+      ra.len.push_back(b->h_slen[rid]);
+      ra.id.push_back(rid);
+      ra.base.push_back(rb_off[f] + (int64_t)(rid - b->S[f] - 1) * ld[f] - b->S[f]);
+    }
+    const int32_t rid_last = rows[j - 1].rid;
+    const int32_t g0 = (int32_t)(b->S[f] / kGroup);
+    if (!wpp) {
+      for (int32_t g = g0; g * kGroup < rid_last; g += 4) items.push_back(make_int4(e0, (int)(j - i), g, 0));
+    } else {
+      for (int32_t c = (int32_t)b->S[f]; c < rid_last; c += kWppCols) items.push_back(make_int4(e0, 1, c / kGroup, 0));
+    }
+    i = j;
+  }
+}
+
+static KParams batch_params(const Batch *b, uint16_t *rowbuf) {
+  KParams p = {};
+  p.peq = b->d_peq;
+  p.colres = b->d_colres;
+  p.group_off = b->d_group_off;
+  p.group_chunks = b->d_group_chunks;
+  p.col_perm = b->d_perm;
+  p.col_len = b->d_slen;
+  p.n_cols = (int32_t)b->Kpad;
+  p.n_groups = b->n_groups;
+  p.mode = kOutBatch;
+  p.out = rowbuf;
+  p.triangle = 1;
+  return p;
+}
+
+// ---- the autotuner: rows per thread-per-pair tile, per kernel width.  The
+// first batch with enough rows of a width times each allowed R on the same
+// sample of its rows (identical work) and keeps the fastest for the process
+// (the single-family launch planner uses it too).
+static std::mutex g_tune_mu;
+static bool g_tuned[kTppMaxW + 1] = {false};
+static std::atomic<int> g_autotune{1};
+constexpr size_t kTuneMinRows = 64, kTuneSampleRows = 1024;
+
+static cudaError_t time_rows(const Batch *b, uint16_t *rowbuf, const std::vector<BRow> &rows, size_t count,
+                             int W, int R, const std::vector<int64_t> &h_peq_off,
+                             const std::vector<int64_t> &rb_off, const std::vector<int64_t> &ld,
+                             cudaStream_t st, float *ms) {
+  RowArrays ra;
+  std::vector<int4> items;
+  append_rows(b, rows, count, false, R, h_peq_off, rb_off, ld, ra, items);
+  int64_t *d_peq = nullptr, *d_base = nullptr;
+  int32_t *d_len = nullptr, *d_id = nullptr;
+  int4 *d_items = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = dev_alloc((void **)&d_peq, sizeof(int64_t) * ra.peq.size());
+  if (err == cudaSuccess) err = dev_alloc((void **)&d_base, sizeof(int64_t) * ra.base.size());
+  if (err == cudaSuccess) err = dev_alloc((void **)&d_len, sizeof(int32_t) * ra.len.size());
+  if (err == cudaSuccess) err = dev_alloc((void **)&d_id, sizeof(int32_t) * ra.id.size());
+  if (err == cudaSuccess) err = dev_alloc((void **)&d_items, sizeof(int4) * items.size());
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_peq, ra.peq.data(), sizeof(int64_t) * ra.peq.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_base, ra.base.data(), sizeof(int64_t) * ra.base.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_len, ra.len.data(), sizeof(int32_t) * ra.len.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_id, ra.id.data(), sizeof(int32_t) * ra.id.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) {
+    KParams p = batch_params(b, rowbuf);
+    p.row_peq_off = d_peq;
+    p.row_len = d_len;
+    p.row_id = d_id;
+    p.row_base = d_base;
+    p.items = d_items;
+    p.e0 = 0;
+    p.e1 = (int32_t)ra.id.size();
+    const dim3 grid((unsigned)items.size());
+    err = launch_tpp(W, R, p, grid, st);  // warm-up
+    if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+    for (int i = 0; i < 2 && err == cudaSuccess; ++i) err = launch_tpp(W, R, p, grid, st);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dev_free(d_peq); dev_free(d_base); dev_free(d_len); dev_free(d_id); dev_free(d_items);
+  return err;
+}
+
+// autotune rows per tile for the widths of this batch not tuned yet in this process
+static cudaError_t autotune_rows(Batch *b, uint16_t *rowbuf, const std::vector<Bucket> &buckets,
+                                 const std::vector<std::vector<BRow>> &rows_by_bucket,
+                                 const std::vector<int64_t> &h_peq_off, const std::vector<int64_t> &rb_off,
+                                 const std::vector<int64_t> &ld, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (size_t bk = 0; bk < buckets.size(); ++bk) {
+    const Bucket &B = buckets[bk];
+    const auto &rows = rows_by_bucket[bk];
+    if (B.wpp || g_tuned[B.kw] || rows.size() < kTuneMinRows) continue;
+    const size_t count = std::min(rows.size(), kTuneSampleRows);
+    int best_R = tpp_default_rows(B.kw);
+    float best_ms = 0.f;
+    bool any = false;
+    for (int R : {1, 2, 4}) {
+      if (!tpp_rows_allowed(B.kw, R)) continue;
+      float ms = 0.f;
+      const cudaError_t e = time_rows(b, rowbuf, rows, count, B.kw, R, h_peq_off, rb_off, ld, st, &ms);
+      if (e != cudaSuccess) return e;
+      if (!any || ms < best_ms) { best_ms = ms; best_R = R; any = true; }
+    }
+    set_tpp_rows(B.kw, best_R);
+    g_tuned[B.kw] = true;
+    b->stats[10] += 1;
+  }
+  b->stats[11] = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+  return cudaSuccess;
+}
 
 static int batch_plan(Batch *b, cudaStream_t st) {
   AllocStream alloc_on(st);
   const int32_t F = b->F;
+  RowArrays ra;  // row entries of every bucket, concatenated
   Arena A{&b->plan_mem};
   cudaError_t err = cudaSuccess;
   const int T = 256;
@@ -370,8 +513,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   std::vector<std::vector<int64_t>> e_peq(1), e_base(1);
   std::vector<std::vector<int32_t>> e_len(1), e_id(1);
   // first pass: which rows go to which bucket, in order
-  struct Row { int32_t rid; int32_t f; };
-  std::vector<std::vector<Row>> rows_by_bucket;
+  std::vector<std::vector<BRow>> rows_by_bucket;
   int64_t cells = 0, words = 0, pairs = 0;
   std::vector<int64_t> h_peq_off(b->Kpad + 1, 0);
   for (int64_t s = 0; s < b->Kpad; ++s) h_peq_off[s + 1] = h_peq_off[s] + (b->h_slen[s] + 63) / 64;
@@ -389,39 +531,21 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       if (n == 0) continue;
       const int bk = bucket_for(W);
       if ((int)rows_by_bucket.size() <= bk) rows_by_bucket.resize(bk + 1);
-      rows_by_bucket[bk].push_back(Row{rid, f});
+      rows_by_bucket[bk].push_back(BRow{rid, f});
     }
   }
+  // the row blocks (the autotuner's trial launches write into them too)
+  cudaError_t pre_err = cudaSuccess;
+  uint16_t *rowbuf = A.get<uint16_t>((size_t)rb_off[F]);
+  if (A.err != cudaSuccess) pre_err = A.err;
+  if (pre_err == cudaSuccess && g_autotune.load())
+    pre_err = autotune_rows(b, rowbuf, buckets, rows_by_bucket, h_peq_off, rb_off, ld, st);
   // second pass: row arrays and work items
-  std::vector<int64_t> r_peq, r_base;
-  std::vector<int32_t> r_len, r_id;
   for (size_t bk = 0; bk < buckets.size(); ++bk) {
     Bucket &B = buckets[bk];
-    const auto &rows = rows_by_bucket[bk];
-    const int R = B.wpp ? 1 : tpp_R(B.kw);
-    size_t i = 0;
-    while (i < rows.size()) {
-      const int32_t f = rows[i].f;
-      size_t j = i + 1;
-      while (j < rows.size() && j - i < (size_t)R && rows[j].f == f) ++j;
-      const int32_t e0 = (int32_t)r_id.size();
-      for (size_t q = i; q < j; ++q) {
-        const int32_t rid = rows[q].rid;
-        r_peq.push_back(h_peq_off[rid]);
-        r_len.push_back(b->h_slen[rid]);
-        r_id.push_back(rid);
-        r_base.push_back(rb_off[f] + (int64_t)(rid - b->S[f] - 1) * ld[f] - b->S[f]);
-      }
-      const int32_t rid_last = rows[j - 1].rid;
-      const int32_t g0 = (int32_t)(b->S[f] / kGroup);
-      if (!B.wpp) {
-        for (int32_t g = g0; g * kGroup < rid_last; g += 4) B.items.push_back(make_int4(e0, (int)(j - i), g, 0));
-      } else {
-        for (int32_t c = (int32_t)b->S[f]; c < rid_last; c += kWppCols)
-          B.items.push_back(make_int4(e0, 1, c / kGroup, 0));
-      }
-      i = j;
-    }
+    B.R = B.wpp ? 1 : tpp_rows(B.kw);
+    append_rows(b, rows_by_bucket[bk], rows_by_bucket[bk].size(), B.wpp, B.R, h_peq_off, rb_off, ld, ra,
+                B.items);
   }
   int64_t n_items = 0;
   for (auto &B : buckets) n_items += (int64_t)B.items.size();
@@ -440,9 +564,8 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     all_items.insert(all_items.end(), buckets[bk].items.begin(), buckets[bk].items.end());
   }
   int4 *d_items = nullptr;
-  uint16_t *rowbuf = nullptr;
   std::vector<SmemArgs> smem_args[5];  // cluster sizes 1, 2, 4, 8, 16
-  int32_t smem_P[5] = {0, 0, 0, 0, 0};
+  size_t smem_dyn[5] = {0, 0, 0, 0, 0};
   struct GlobalFam { SlinkState S; int64_t off, ld; int32_t k; };
   std::vector<GlobalFam> global_fams;
   std::vector<BatchInit> inits;
@@ -456,12 +579,12 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   SmemArgs *d_sargs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   const int max_cl = max_cluster_global();
 
-  BCK(upload_vec(A, r_peq, &d_rpeq, st));
-  BCK(upload_vec(A, r_base, &d_rbase, st));
-  BCK(upload_vec(A, r_len, &d_rlen, st));
-  BCK(upload_vec(A, r_id, &d_rid, st));
+  BCK(pre_err);
+  BCK(upload_vec(A, ra.peq, &d_rpeq, st));
+  BCK(upload_vec(A, ra.base, &d_rbase, st));
+  BCK(upload_vec(A, ra.len, &d_rlen, st));
+  BCK(upload_vec(A, ra.id, &d_rid, st));
   BCK(upload_vec(A, all_items, &d_items, st));
-  rowbuf = A.get<uint16_t>((size_t)rb_off[F]);
   // outputs (whole batch)
   b->d_pi = A.get<int32_t>(b->N);
   b->d_lnum = A.get<uint64_t>(b->N);
@@ -524,9 +647,11 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       a.r0 = 1;
       a.r1 = k;
       a.P = (k + cl - 1) / cl;
+      a.sshift = smem_sample_shift(a.P, a.P * cl);
       a.batch = nullptr;
+      a.dyn_bytes = 0;
       smem_args[ci].push_back(a);
-      smem_P[ci] = std::max(smem_P[ci], a.P);
+      smem_dyn[ci] = std::max(smem_dyn[ci], smem_dyn_bytes(a.P, a.P * cl, a.sshift));
     } else {
       global_fams.push_back(GlobalFam{S, rb_off[f], ld[f], k});
     }
@@ -571,34 +696,19 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     {
       cudaError_t e = cudaEventRecordWithFlags(b->tev[0], b->cap, cudaEventRecordExternal);
       // stage I: every family's triangle, one launch per kernel width
-      KParams p = {};
-      p.peq = b->d_peq;
+      KParams p = batch_params(b, rowbuf);
       p.row_peq_off = d_rpeq;
       p.row_len = d_rlen;
       p.row_id = d_rid;
-      p.row_orig = nullptr;
-      p.colres = b->d_colres;
-      p.group_off = b->d_group_off;
-      p.group_chunks = b->d_group_chunks;
-      p.col_perm = b->d_perm;
-      p.col_len = b->d_slen;
-      p.n_cols = (int32_t)b->Kpad;
-      p.n_groups = b->n_groups;
-      p.mode = kOutBatch;
-      p.out = rowbuf;
-      p.ld = 0;
-      p.row0 = 0;
-      p.k = 0;
-      p.triangle = 1;
       p.row_base = d_rbase;
       for (size_t bk = 0; bk < buckets.size() && e == cudaSuccess; ++bk) {
         const int64_t n = item_off[bk + 1] - item_off[bk];
         if (n == 0) continue;
         p.items = d_items + item_off[bk];
         p.e0 = 0;
-        p.e1 = (int32_t)r_id.size();
+        p.e1 = (int32_t)ra.id.size();
         e = buckets[bk].wpp ? launch_wpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap)
-                            : launch_tpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap);
+                            : launch_tpp(buckets[bk].kw, buckets[bk].R, p, dim3((unsigned)n), b->cap);
         ++launches;
       }
       // stage II: one cluster per family
@@ -612,7 +722,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       }
       for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
         if (smem_args[ci].empty()) continue;
-        e = launch_slink_smem_batch(d_sargs[ci], (int32_t)smem_args[ci].size(), 1 << ci, smem_P[ci],
+        e = launch_slink_smem_batch(d_sargs[ci], (int32_t)smem_args[ci].size(), 1 << ci, smem_dyn[ci],
                                     narrow, b->cap);
         ++launches;
       }
@@ -744,3 +854,12 @@ void famsa_batch_free(famsa_batch *bh) {
 }
 
 }  // extern "C"
+
+extern "C" int famsa_debug_set_autotune(int on) {
+  famsa::g_autotune.store(on ? 1 : 0);
+  if (!on) {
+    std::lock_guard<std::mutex> lk(famsa::g_tune_mu);
+    for (int w = 1; w <= famsa::kTppMaxW; ++w) famsa::g_tuned[w] = false;
+  }
+  return FAMSA_OK;
+}

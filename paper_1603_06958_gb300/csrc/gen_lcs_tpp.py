@@ -1,0 +1,44 @@
+"""Generate lcs_tpp_{a,b,c,d}.cu: the thread-per-pair LCS kernel instantiated
+for every (W, R) the launch planner and the batch autotuner may pick
+(W = 1..32 words, R in {1, 2, 4} rows per tile with R * W <= 32), split over
+four translation units so they compile in parallel.
+
+Run: python gen_lcs_tpp.py   (writes the four files next to this script)
+"""
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+UNITS = {"a": range(1, 9), "b": range(9, 17), "c": range(17, 25), "d": range(25, 33)}
+
+
+def rows_for(W):
+    return [R for R in (1, 2, 4) if R * W <= 32]
+
+
+def unit(name, widths):
+    lines = ["// Generated by gen_lcs_tpp.py -- do not edit.",
+             "// Thread-per-pair LCS kernels for row widths W = %d..%d (64-bit words)," % (widths[0], widths[-1]),
+             "// R rows per tile.",
+             '#include "lcs_kernels.cuh"', "", "namespace famsa {", "",
+             "template <int W, int R>",
+             "static cudaError_t go(const KParams &p, dim3 grid, cudaStream_t st) {",
+             "  size_t smem = (size_t)R * W * kPeqWordU32 * sizeof(uint32_t);",
+             "  k_lcs_tpp<W, R><<<grid, kTppThreads, smem, st>>>(p);",
+             "  return cudaGetLastError();", "}", "",
+             "cudaError_t launch_tpp_%s(int W, int R, const KParams &p, dim3 grid, cudaStream_t st) {" % name,
+             "  switch (W * 8 + R) {"]
+    for W in widths:
+        for R in rows_for(W):
+            lines.append("    case %d: return go<%d, %d>(p, grid, st);" % (W * 8 + R, W, R))
+    lines += ["    default: return cudaErrorInvalidValue;", "  }", "}", "", "}  // namespace famsa", ""]
+    return "\n".join(lines)
+
+
+def main():
+    for name, ws in UNITS.items():
+        with open(os.path.join(HERE, "lcs_tpp_%s.cu" % name), "w") as f:
+            f.write(unit(name, list(ws)))
+
+
+if __name__ == "__main__":
+    main()

@@ -7,20 +7,34 @@
 
 namespace famsa {
 
-cudaError_t launch_tpp_a(int W, const KParams &p, dim3 grid, cudaStream_t st);
-cudaError_t launch_tpp_b(int W, const KParams &p, dim3 grid, cudaStream_t st);
-cudaError_t launch_tpp_c(int W, const KParams &p, dim3 grid, cudaStream_t st);
+cudaError_t launch_tpp_a(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
+cudaError_t launch_tpp_b(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
+cudaError_t launch_tpp_c(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
+cudaError_t launch_tpp_d(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
 
-cudaError_t launch_tpp(int W, const KParams &p, dim3 grid, cudaStream_t st) {
-  if (W <= 10) return launch_tpp_a(W, p, grid, st);
-  if (W <= 20) return launch_tpp_b(W, p, grid, st);
-  return launch_tpp_c(W, p, grid, st);
+cudaError_t launch_tpp(int W, int R, const KParams &p, dim3 grid, cudaStream_t st) {
+  if (W < 1 || W > kTppMaxW || !tpp_rows_allowed(W, R)) return cudaErrorInvalidValue;
+  if (W <= 8) return launch_tpp_a(W, R, p, grid, st);
+  if (W <= 16) return launch_tpp_b(W, R, p, grid, st);
+  if (W <= 24) return launch_tpp_c(W, R, p, grid, st);
+  return launch_tpp_d(W, R, p, grid, st);
+}
+
+// rows per tile for each width (0 = the default); the batch autotuner writes it
+static std::atomic<int> g_tpp_rows[kTppMaxW + 1];
+
+int tpp_rows(int W) {
+  const int r = (W >= 1 && W <= kTppMaxW) ? g_tpp_rows[W].load() : 0;
+  return r ? r : tpp_default_rows(W);
+}
+
+void set_tpp_rows(int W, int R) {
+  if (W >= 1 && W <= kTppMaxW && (R == 0 || tpp_rows_allowed(W, R))) g_tpp_rows[W].store(R);
 }
 
 // Rows wider than this use warp-per-pair (tests lower it to exercise that path).
 static std::atomic<int> g_tpp_max_w{kTppMaxW};
 
-static int tpp_rows(int W) { return W <= 4 ? 4 : (W <= 8 ? 2 : 1); }
 static int wpp_nw(int W) {
   int nw = 1;
   while (32 * nw < W) nw *= 2;
@@ -72,7 +86,7 @@ cudaError_t launch_lcs(const LcsBatch &b, cudaStream_t st, int64_t *launches) {
       if (!wpp) {
         int R = tpp_rows(kw);
         dim3 grid((unsigned)((e1 - e0 + R - 1) / R), (unsigned)((col_bound + kTppThreads - 1) / kTppThreads));
-        err = launch_tpp(kw, p, grid, st);
+        err = launch_tpp(kw, R, p, grid, st);
       } else {
         dim3 grid((unsigned)(e1 - e0), (unsigned)((col_bound + kWppCols - 1) / kWppCols));
         err = launch_wpp(kw, p, grid, st);
@@ -91,4 +105,15 @@ extern "C" int famsa_debug_set_tpp_max_w(int w) {
   if (w < 0 || w > famsa::kTppMaxW) return FAMSA_EINVAL;
   famsa::g_tpp_max_w.store(w);
   return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_set_tpp_rows(int w, int r) {
+  if (w < 1 || w > famsa::kTppMaxW || (r != 0 && !famsa::tpp_rows_allowed(w, r))) return FAMSA_EINVAL;
+  famsa::set_tpp_rows(w, r);
+  return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_tpp_rows(int w) {
+  if (w < 1 || w > famsa::kTppMaxW) return -1;
+  return famsa::tpp_rows(w);
 }

@@ -48,10 +48,10 @@ constexpr int kTppThreads = 128;  // 4 warps = 4 column groups per CTA
 constexpr int kWppThreads = 256;  // 8 warps, one column each at a time
 constexpr int kWppCols = 64;      // columns per warp-per-pair CTA
 
-template <int W>
-struct TppRows {
-  static constexpr int R = W <= 4 ? 4 : (W <= 8 ? 2 : 1);
-};
+// Rows per thread-per-pair tile: the default, and the choices the batch
+// autotuner may take (R * W <= 32 keeps the R x 2W words of V in registers).
+constexpr int tpp_default_rows(int W) { return W <= 4 ? 4 : (W <= 8 ? 2 : 1); }
+constexpr bool tpp_rows_allowed(int W, int R) { return (R == 1 || R == 2 || R == 4) && R * W <= 32; }
 
 __device__ __forceinline__ int64_t tri_index(int64_t i, int64_t j, int64_t k) {
   return i * k - i * (i + 1) / 2 + (j - i - 1);
@@ -98,9 +98,8 @@ __device__ __forceinline__ void emit_lcs(const KParams &p, int32_t e, int32_t ri
 // recurrence for all R rows of the tile at once (R independent carry chains).
 // With a work list (batched families), work item blockIdx.x names the tile
 // (at most R rows of one family) and its first column group instead.
-template <int W>
+template <int W, int R>
 __global__ void __launch_bounds__(kTppThreads) k_lcs_tpp(KParams p) {
-  constexpr int R = TppRows<W>::R;
   extern __shared__ __align__(16) uint32_t sPeq[];  // R * W * 64 u32
   int32_t tile_e, tile_end, gbase;
   if (p.items) {
@@ -258,7 +257,11 @@ __global__ void __launch_bounds__(kWppThreads) k_lcs_wpp(KParams p) {
 }
 
 // per-width launchers (defined in the lcs_tpp_*.cu / lcs_wpp.cu units)
-cudaError_t launch_tpp(int W, const KParams &p, dim3 grid, cudaStream_t st);
+// thread-per-pair launch with R rows per tile (tpp_rows_allowed(W, R))
+cudaError_t launch_tpp(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
+// the R the launch planner uses for width W (autotuned, else the default)
+int tpp_rows(int W);
+void set_tpp_rows(int W, int R);
 cudaError_t launch_wpp(int NW, const KParams &p, dim3 grid, cudaStream_t st);
 
 }  // namespace famsa

@@ -1,30 +1,27 @@
-// Thread-per-pair LCS kernels for row widths W = 21..32 (64-bit words).
+// Generated by gen_lcs_tpp.py -- do not edit.
+// Thread-per-pair LCS kernels for row widths W = 17..24 (64-bit words),
+// R rows per tile.
 #include "lcs_kernels.cuh"
 
 namespace famsa {
 
-template <int W>
+template <int W, int R>
 static cudaError_t go(const KParams &p, dim3 grid, cudaStream_t st) {
-  constexpr int R = TppRows<W>::R;
   size_t smem = (size_t)R * W * kPeqWordU32 * sizeof(uint32_t);
-  k_lcs_tpp<W><<<grid, kTppThreads, smem, st>>>(p);
+  k_lcs_tpp<W, R><<<grid, kTppThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tpp_c(int W, const KParams &p, dim3 grid, cudaStream_t st) {
-  switch (W) {
-    case 21: return go<21>(p, grid, st);
-    case 22: return go<22>(p, grid, st);
-    case 23: return go<23>(p, grid, st);
-    case 24: return go<24>(p, grid, st);
-    case 25: return go<25>(p, grid, st);
-    case 26: return go<26>(p, grid, st);
-    case 27: return go<27>(p, grid, st);
-    case 28: return go<28>(p, grid, st);
-    case 29: return go<29>(p, grid, st);
-    case 30: return go<30>(p, grid, st);
-    case 31: return go<31>(p, grid, st);
-    case 32: return go<32>(p, grid, st);
+cudaError_t launch_tpp_c(int W, int R, const KParams &p, dim3 grid, cudaStream_t st) {
+  switch (W * 8 + R) {
+    case 137: return go<17, 1>(p, grid, st);
+    case 145: return go<18, 1>(p, grid, st);
+    case 153: return go<19, 1>(p, grid, st);
+    case 161: return go<20, 1>(p, grid, st);
+    case 169: return go<21, 1>(p, grid, st);
+    case 177: return go<22, 1>(p, grid, st);
+    case 185: return go<23, 1>(p, grid, st);
+    case 193: return go<24, 1>(p, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -89,6 +89,9 @@ __device__ __forceinline__ Clamp shfl_clamp_up(const Clamp &c, int d) {
 __device__ __forceinline__ Clamp shfl_clamp_down(const Clamp &c, int d) {
   return Clamp{__shfl_down_sync(0xffffffffu, c.lo, d), __shfl_down_sync(0xffffffffu, c.hi, d)};
 }
+__device__ __forceinline__ Clamp shfl_clamp_idx(const Clamp &c, int src) {
+  return Clamp{__shfl_sync(0xffffffffu, c.lo, src), __shfl_sync(0xffffffffu, c.hi, src)};
+}
 
 // Block-level exclusive scans of clamps, forward (thread order) and backward
 // (reverse thread order) at once.  sw needs 4*32+2 entries.  Returns the
@@ -239,11 +242,15 @@ struct SmemArgs {
   int64_t ld;  // even, so every row starts on a 4-byte boundary
   int32_t r0, r1;
   int32_t P;   // positions per CTA
+  int32_t sshift;  // every 2^sshift-th D is sampled for the run-merge searches
   // batched families: cluster c takes batch[c] (its own state, rows and sizes)
   const SmemArgs *batch;
+  size_t dyn_bytes;  // batched launch: dynamic shared memory of every cluster
 };
-cudaError_t launch_slink_smem_batch(const SmemArgs *d_args, int32_t n_clusters, int cl, int32_t Pmax,
+cudaError_t launch_slink_smem_batch(const SmemArgs *d_args, int32_t n_clusters, int cl, size_t dyn_bytes,
                                     bool narrow, cudaStream_t st);
+size_t smem_dyn_bytes(int32_t P, int32_t k, int shift);
+int smem_sample_shift(int32_t P, int32_t k);
 
 struct FinBufs {
   int32_t *idx, *posof, *it, *rt, *pi, *sub_lo, *sub_hi, *ordA, *ordB, *rank, *sorder, *merges,
@@ -259,7 +266,6 @@ cudaError_t launch_finalize(const int32_t *ord, const uint64_t *gap, const int32
 cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
                                 int32_t r1, int cl, cudaStream_t st);
 int max_cluster_global();
-size_t smem_bytes_for(int32_t P);
 int smem_cluster_for(int32_t k, int force);
 cudaError_t launch_slink_smem(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
                               int32_t r1, int cl, int32_t k, bool narrow, cudaStream_t st);

@@ -29,17 +29,36 @@ constexpr int kSmemThreads = 512;
 constexpr size_t kSmemBytesPerPos = 6 * sizeof(uint64_t) + 9 * sizeof(int32_t);
 constexpr int kLocalRuns = 16;     // run starts a CTA may hold per side (fast merge)
 constexpr int kFastRuns = 16;      // runs per side the fast merge handles
-constexpr int kSampleShift = 4;    // every 16th D value is sampled for the merge searches
-constexpr int kMaxSamples = 3072;  // k <= 49152
+constexpr size_t kStaticSmem = 24 * 1024;  // the kernel's static shared memory, with margin
 
-size_t smem_bytes_for(int32_t P) { return (size_t)P * kSmemBytesPerPos; }
+// Dynamic shared memory: the per-position state, then every 2^shift-th D value
+// of the whole order (the samples of the run-merge rank search).
+size_t smem_dyn_bytes(int32_t P, int32_t k, int shift) {
+  return (((size_t)P * kSmemBytesPerPos + 7) & ~(size_t)7) +
+         (size_t)((k + (1 << shift) - 1) >> shift) * sizeof(uint64_t);
+}
+
+// The sample stride (16 .. 64) whose samples fit beside the state of P
+// positions, or -1 when even the state does not fit.  Finer strides shorten
+// the DSMEM searches of a run merge but cost more in gathering the samples
+// from every CTA (stride 4 measured slower than 16 at k = 20,000).
+int smem_sample_shift(int32_t P, int32_t k) {
+  int device = 0, optin = 0;
+  cudaGetDevice(&device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  for (int s = 4; s <= 6; ++s)
+    if (smem_dyn_bytes(P, k, s) + kStaticSmem <= (size_t)optin) return s;
+  return -1;
+}
 
 struct Slot {
-  uint64_t aggL_lo, aggL_hi, aggR_lo, aggR_hi;  // scan totals of this CTA
-  uint64_t arg_key, first_D, last_D;            // phase B results
-  int32_t arg_pos, min_asc, max_desc;
   int32_t cnt_a, cnt_b;                         // local run starts (fast merge)
   int32_t run_a[kLocalRuns], run_b[kLocalRuns];
+};
+// phase B results of one CTA, pushed into every CTA of the cluster
+struct BRes {
+  uint64_t arg_key, first_D, last_D;
+  int32_t arg_pos, min_asc, max_desc, pad;
 };
 
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
@@ -81,6 +100,10 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
   int32_t *const raw = ibase + 6 * P;   // aligned 32-bit words holding next-row LCS values
   int32_t *const raw2 = ibase + 7 * P;  // next-row LCS values after a run merge
   int32_t *const nold = ibase + 8 * P;  // old position of each new position after a run merge
+  // every 2^sshift-th D of the whole order, for the rank searches of a run merge
+  uint64_t *const sSmp = reinterpret_cast<uint64_t *>(
+      reinterpret_cast<char *>(smem) + (((size_t)P * kSmemBytesPerPos + 7) & ~(size_t)7));
+  const int sshift = a.sshift;
 #define gapS(b) (gap0 + (b) * P)
 #define lamS(b) (lam0 + (b) * P)
 #define ordS(b) (ord0 + (b) * P)
@@ -89,9 +112,12 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
 #define XS(b) (X0 + (b) * P)
   __shared__ Clamp sw[130];
   __shared__ Slot slot;
+  // every CTA's scan totals and phase B results, written here by the CTA that
+  // owns them (DSMEM stores before a cluster barrier) and read locally after it
+  __shared__ Clamp sAggL[kMaxClusterCtas], sAggR[kMaxClusterCtas];
+  __shared__ BRes sRes[kMaxClusterCtas];
   __shared__ Clamp sPre[2];
   __shared__ int32_t sRunsA[kRunsSmem], sRunsB[kRunsSmem];
-  __shared__ uint64_t sSmp[kMaxSamples];
   __shared__ uint64_t sRed[32];
   __shared__ int32_t sRedPos[32], sRedA[32], sRedD[32];
   __shared__ int32_t sX0, sViol, sRawN, sFast, sNA, sNB;
@@ -123,11 +149,9 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
     }
     Clamp totL, totR;
     block_scan2<K>(sl, sr, &preL, &preR, &totL, &totR, sw);
-    if (threadIdx.x == 0) {
-      slot.aggL_lo = totL.lo;
-      slot.aggL_hi = totL.hi;
-      slot.aggR_lo = totR.lo;
-      slot.aggR_hi = totR.hi;
+    if (threadIdx.x < ncta) {
+      cluster.map_shared_rank(sAggL, (int)threadIdx.x)[cta] = totL;
+      cluster.map_shared_rank(sAggR, (int)threadIdx.x)[cta] = totR;
     }
   };
 
@@ -185,9 +209,8 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
     if (warp == 0) {
       Clamp aL = identity_clamp<K>(), aR = identity_clamp<K>();
       if (lane < ncta) {
-        const Slot *o = cluster.map_shared_rank(&slot, lane);
-        aL = Clamp{o->aggL_lo, o->aggL_hi};
-        aR = Clamp{o->aggR_lo, o->aggR_hi};
+        aL = sAggL[lane];
+        aR = sAggR[lane];
       }
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -263,14 +286,15 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
         masc = min(masc, __shfl_down_sync(0xffffffffu, masc, d));
         mdesc = max(mdesc, __shfl_down_sync(0xffffffffu, mdesc, d));
       }
-      if (lane == 0) {
-        slot.arg_key = best;
-        slot.arg_pos = bestpos;
-        slot.min_asc = masc;
-        slot.max_desc = mdesc;
-        slot.first_D = mc > 0 ? DD[0] : INF;
-        slot.last_D = mc > 0 ? DD[mc - 1] : INF;
-      }
+      BRes rr;
+      rr.arg_key = __shfl_sync(0xffffffffu, best, 0);
+      rr.arg_pos = __shfl_sync(0xffffffffu, bestpos, 0);
+      rr.min_asc = __shfl_sync(0xffffffffu, masc, 0);
+      rr.max_desc = __shfl_sync(0xffffffffu, mdesc, 0);
+      rr.first_D = mc > 0 ? DD[0] : INF;
+      rr.last_D = mc > 0 ? DD[mc - 1] : INF;
+      rr.pad = 0;
+      if (lane < ncta) cluster.map_shared_rank(sRes, lane)[cta] = rr;
     }
     SUBT(2)
     cluster.sync();
@@ -282,13 +306,13 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
       uint64_t b = INF, f = INF, l = INF;
       int32_t bp = INT32_MAX, ma = INT32_MAX, md = -1;
       if (lane < ncta) {
-        const Slot *o = cluster.map_shared_rank(&slot, lane);
-        b = o->arg_key;
-        bp = o->arg_pos;
-        ma = o->min_asc;
-        md = o->max_desc;
-        f = o->first_D;
-        l = o->last_D;
+        const BRes &o = sRes[lane];
+        b = o.arg_key;
+        bp = o.arg_pos;
+        ma = o.min_asc;
+        md = o.max_desc;
+        f = o.first_D;
+        l = o.last_D;
       }
       // the pair across the boundary between CTA lane-1 and CTA lane
       const uint64_t prevLast = __shfl_up_sync(0xffffffffu, l, 1);
@@ -432,8 +456,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
         }
         const int32_t ta = __shfl_sync(0xffffffffu, pa, 31), tb = __shfl_sync(0xffffffffu, pb, 31);
         const int32_t nA = x0 > 0 ? 1 + ta : 0, nB = 1 + tb;
-        const bool fast = !over && nA <= kFastRuns && nB <= kFastRuns &&
-                          ((m + (1 << kSampleShift) - 1) >> kSampleShift) <= kMaxSamples;
+        const bool fast = !over && nA <= kFastRuns && nB <= kFastRuns;
         if (fast && lane < ncta) {
           const Slot *o = cluster.map_shared_rank(&slot, lane);
           for (int t = 0; t < ca; ++t) sRunsA[1 + pa - ca + t] = o->run_a[t];
@@ -453,8 +476,8 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
         if (tid == 0) { ctl[kCtlStats + 6] += 1; ctl[kCtlStats + 7] += sNA + sNB; }
         SUBT(9)
         const int32_t nA = sNA, nB = sNB;
-        const int32_t nsmp = (m + (1 << kSampleShift) - 1) >> kSampleShift;
-        for (int32_t q = threadIdx.x; q < nsmp; q += T) sSmp[q] = getD(q << kSampleShift);
+        const int32_t nsmp = (m + (1 << sshift) - 1) >> sshift;
+        for (int32_t q = threadIdx.x; q < nsmp; q += T) sSmp[q] = getD(q << sshift);
         __syncthreads();
         SUBT(12)
         // ---- each element's place in the stable merge of its side
@@ -476,18 +499,18 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
               if (left) return r2 < r ? !K::lt(w, v) : K::lt(v, w);
               return r2 < r ? !K::lt(v, w) : K::lt(w, v);
             };
-            // samples at positions q*16 inside [s0, e0)
-            constexpr int32_t kStride = 1 << kSampleShift;
-            int32_t qa = (s0 + kStride - 1) >> kSampleShift, qb = (e0 - 1) >> kSampleShift;
+            // samples at positions q * 2^sshift inside [s0, e0)
+            const int32_t kStride = 1 << sshift;
+            int32_t qa = (s0 + kStride - 1) >> sshift, qb = (e0 - 1) >> sshift;
             int32_t lo = qa, hi = qb + 1;  // first sample index with before() false
             while (lo < hi) {
               const int32_t mid = (lo + hi) >> 1;
               if (before(sSmp[mid])) lo = mid + 1; else hi = mid;
             }
             // the boundary lies in [wlo, whi): after the last true sample, up to the first false one
-            const int32_t wlo = lo > qa ? ((lo - 1) << kSampleShift) + 1 : s0;
-            const int32_t whi = lo <= qb ? (lo << kSampleShift) : e0;
-            // binary search inside the window (fewer than 16 positions) through DSMEM
+            const int32_t wlo = lo > qa ? ((lo - 1) << sshift) + 1 : s0;
+            const int32_t whi = lo <= qb ? (lo << sshift) : e0;
+            // binary search inside the window (fewer than 2^sshift positions) through DSMEM
             int32_t wa = wlo, wb = whi;
             while (wa < wb) {
               const int32_t mid = (wa + wb) >> 1;
@@ -683,15 +706,14 @@ int smem_cluster_for(int32_t k, int force) {
   int device = 0, optin = 0;
   cudaGetDevice(&device);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  const size_t static_bytes = 52 * 1024;
-  if (((k + (1 << kSampleShift) - 1) >> kSampleShift) > kMaxSamples) return 0;
+  (void)optin;
   // the smallest cluster that fits, but at least 16 CTAs from 16k points on
   // (per-insertion work then dominates the barrier cost)
   for (int c : {1, 2, 4, 8, 16}) {
     if (force && c != force) continue;
     if (!force && k >= 16384 && c < 16) continue;
     int32_t P = (k + c - 1) / c;
-    if (smem_bytes_for(P) + static_bytes <= (size_t)optin) return c;
+    if (smem_sample_shift(P, P * c) >= 0) return c;
   }
   return 0;
 }
@@ -721,7 +743,7 @@ static cudaError_t smem_kernel_attributes() {
 
 template <class K>
 static cudaError_t launch_smem_t(const SmemArgs &args, int cl, cudaStream_t st, int32_t n_clusters) {
-  const size_t dyn = smem_bytes_for(args.P);
+  const size_t dyn = args.batch ? args.dyn_bytes : smem_dyn_bytes(args.P, args.P * cl, args.sshift);
   cudaError_t e = smem_kernel_attributes<K>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -748,15 +770,18 @@ cudaError_t launch_slink_smem(const SlinkState &S, const uint16_t *rowbuf, int64
   args.r0 = r0;
   args.r1 = r1;
   args.P = (k + cl - 1) / cl;
+  args.sshift = smem_sample_shift(args.P, args.P * cl);
   args.batch = nullptr;
+  args.dyn_bytes = 0;
+  if (args.sshift < 0) return cudaErrorInvalidValue;
   return narrow ? launch_smem_t<KeysNarrow>(args, cl, st, 1) : launch_smem_t<KeysWide>(args, cl, st, 1);
 }
 
-cudaError_t launch_slink_smem_batch(const SmemArgs *d_args, int32_t n_clusters, int cl, int32_t Pmax,
+cudaError_t launch_slink_smem_batch(const SmemArgs *d_args, int32_t n_clusters, int cl, size_t dyn_bytes,
                                     bool narrow, cudaStream_t st) {
   if (n_clusters <= 0) return cudaSuccess;
   SmemArgs args = {};
-  args.P = Pmax;  // sizes the dynamic shared memory of every cluster
+  args.dyn_bytes = dyn_bytes;  // the largest need of the launch's families
   args.batch = d_args;
   return narrow ? launch_smem_t<KeysNarrow>(args, cl, st, n_clusters)
                 : launch_smem_t<KeysWide>(args, cl, st, n_clusters);

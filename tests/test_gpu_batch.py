@@ -76,6 +76,10 @@ def test_batch_small_families_match_oracle_and_alone(fg):
         got = fg.batch_family_tree(out, b, f)
         assert_same(got, oracle.tree(r, o), ("oracle", f))
         assert_same(got, alone(fg, r, o), ("alone", f))
+    # the autotuner's choices are valid rows-per-tile values
+    for w in range(1, 33):
+        r = fg.debug_tpp_rows(w)
+        assert r in (1, 2, 4) and r * w <= 32 or (w > 8 and r == 1)
     # the graph runs again with the same result
     out2 = fg.batch_tree(b)
     for key in KEYS:
@@ -84,12 +88,12 @@ def test_batch_small_families_match_oracle_and_alone(fg):
 
 
 def test_batch_cluster_sizes_and_global_path(fg):
-    # k around 2,600 and 5,000 take 2- and 4-CTA clusters; k = 36,000 exceeds one
+    # k around 2,600 and 5,000 take 2- and 4-CTA clusters; k = 42,000 exceeds one
     # cluster's shared memory and runs the global-memory row update
     fams = [synth.family(2600, 11, root_len=60, alphabet=4),
             synth.family(40, 12, root_len=80),
             synth.family(5000, 13, root_len=40, alphabet=5),
-            synth.family(36000, 14, root_len=12, alphabet=4, sub_rate=0.1)]
+            synth.family(42000, 14, root_len=12, alphabet=4, sub_rate=0.1)]
     res, off, fo = concat(fams)
     b = fg.batch_pack(res, off, fo)
     out = fg.batch_tree(b)

@@ -76,6 +76,20 @@ def test_warp_per_pair_matches(fg, tmax):
         fg.debug_set_tpp_max_w(32)
 
 
+@pytest.mark.parametrize("rows", [1, 2, 4])
+def test_rows_per_tile_choices(fg, rows):
+    # every (width, rows per tile) kernel the autotuner may pick gives the same LCS
+    try:
+        for w in range(1, 33):
+            fg.debug_set_tpp_rows(w, rows if rows * w <= 32 else 0)
+        assert fg.debug_tpp_rows(8) == rows and fg.debug_tpp_rows(16) == (rows if rows * 16 <= 32 else 1)
+        res, off = boundary_family(77, extra=(700, 900, 1500))
+        check_allpairs(fg, res, off)
+    finally:
+        for w in range(1, 33):
+            fg.debug_set_tpp_rows(w, 0)
+
+
 def test_long_sequences_warp_per_pair_default(fg):
     rng = np.random.default_rng(9)
     seqs = [rng.integers(0, 20, n).astype(np.uint8) for n in (2100, 4096, 4097, 6000, 100, 9000)]
