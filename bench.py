@@ -225,6 +225,18 @@ def run_reference(args, rank, world):
     return 0
 
 
+def replica_totals(ms_step, e2e_ms, cells, dist, device):
+    """Replicas (one family per GPU): the slowest rank's step and end-to-end
+    times, and the cells of all ranks."""
+    import torch
+    vals = torch.tensor([ms_step, e2e_ms, cells], dtype=torch.float64, device=device)
+    mx = vals.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = vals.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(tot[2])
+
+
 def concat_families(fams):
     res = np.concatenate([r for r, _ in fams])
     offs, fo, base = [np.zeros(1, np.int64)], [0], 0
@@ -336,12 +348,7 @@ def run_batch(args, rank, world, local_rank):
     d2h = sum(v.nbytes for v in t.values())
     h2d = res.nbytes + off.nbytes
     if dist is not None:
-        vals = torch.tensor([ms_step, float(np.mean(e2e_ms)), cells], dtype=torch.float64, device="cuda")
-        mx = vals.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        tot = vals.clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        ms_max, e2e_max, cells_total = float(mx[0]), float(mx[1]), float(tot[2])
+        ms_max, e2e_max, cells_total = replica_totals(ms_step, float(np.mean(e2e_ms)), cells, dist, "cuda")
     else:
         ms_max, e2e_max, cells_total = ms_step, float(np.mean(e2e_ms)), cells
     if rank != 0:
@@ -587,12 +594,8 @@ def run_ours(args, rank, world, local_rank):
     h2d = res.nbytes + off.nbytes
 
     if dist is not None:
-        vals = torch.tensor([ms_step, float(np.mean(e2e_ms)), cells], dtype=torch.float64, device="cuda")
-        mx = vals.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        tot = vals.clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        ms_step_max, e2e_max, cells_total = float(mx[0]), float(mx[1]), float(tot[2])
+        ms_step_max, e2e_max, cells_total = replica_totals(ms_step, float(np.mean(e2e_ms)), cells, dist,
+                                                          "cuda")
     else:
         ms_step_max, e2e_max, cells_total = ms_step, float(np.mean(e2e_ms)), cells
     if rank != 0:
