@@ -159,29 +159,36 @@ def recorded_traffic():
 
 
 # ------------------------------------------------------------------ CPU baseline
+def random_pairs(k: int, n: int, seed: int):
+    """n seeded uniform random pairs i != j of a family of k sequences."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, k, n)
+    j = rng.integers(0, k - 1, n)
+    j = np.where(j >= i, j + 1, j)
+    return i.astype(np.int32), j.astype(np.int32)
+
+
 def cpu_baseline(res, off, budget_s=15.0):
-    """The oracle's DP LCS, as it stands, on a bounded sample of the workload's rows."""
+    """The oracle's DP LCS, as it stands, on a bounded sample of the workload's
+    pairs: seeded uniform random pairs (the oracle spreads pairs over all host
+    threads), grown until one run takes at least half the budget."""
     import oracle
     k = len(off) - 1
-    lens = np.diff(off).astype(np.int64)
-    prefix = np.concatenate([[0], np.cumsum(lens)])
-    # grow the trailing-row sample until one run takes at least half the budget
-    # (small samples under-use the host threads, so their rate is not extrapolated)
-    rows = 1
+    lens = np.diff(off).astype(np.float64)
+    n = 256
     while True:
-        r0 = k - rows
+        pa, pb = random_pairs(k, n, 12345)
         t0 = time.perf_counter()
-        oracle.lcs_rows(res, off, r0, k)
+        oracle.lcs_pairs(res, off, pa, pb)
         dt = time.perf_counter() - t0
-        if dt >= 0.5 * budget_s or rows >= k - 1:
+        if dt >= 0.5 * budget_s or n >= (1 << 26):
             break
-        rows = int(min(k - 1, rows * max(2.0, 0.75 * budget_s / max(dt, 1e-3))))
-    cells = float(sum(lens[i] * prefix[i] for i in range(r0, k)))
+        n = int(min(1 << 26, n * max(2.0, 0.75 * budget_s / max(dt, 1e-3))))
+    cells = float((lens[pa] * lens[pb]).sum())
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": "DP LCS of rows %d..%d against all earlier sequences (%d pairs, %.3g cells, "
-                      "%.1f s); the O(k) per-row SLINK update is not part of the sample"
-                      % (r0, k - 1, int(sum(range(r0, k))), cells, dt)}
+            "sample": "DP LCS of %d seeded uniform random pairs of the family (%.3g cells, %.1f s); "
+                      "the O(k) per-row SLINK update is not part of the sample" % (n, cells, dt)}
 
 
 # ------------------------------------------------------------------ arms
@@ -192,16 +199,26 @@ def run_reference(args, rank, world):
     res, off = make_family(args.workload, args.seed, args.k)
     k = len(off) - 1
     lens = np.diff(off).astype(np.int64)
-    prefix = np.concatenate([[0], np.cumsum(lens)])
-    rows = max(1, args.ref_rows)
+    # each step: a fresh seeded sample of uniform random pairs, about 2 s of
+    # host work (sized once from a calibration run); the oracle spreads pairs
+    # over all host threads
+    n = 512
+    while True:
+        pa, pb = random_pairs(k, n, 999)
+        t0 = time.perf_counter()
+        oracle.lcs_pairs(res, off, pa, pb)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 or n >= (1 << 24):
+            break
+        n *= 4
+    n = int(max(512, min(1 << 24, n * args.ref_seconds / max(dt, 1e-6))))
     vals, tot_cells, tot_t = [], 0.0, 0.0
     for s in range(args.warmup + args.steps):
-        r1 = k - (s % 8) * rows
-        r0 = max(1, r1 - rows)
+        pa, pb = random_pairs(k, n, 1000 + s)
         t0 = time.perf_counter()
-        oracle.lcs_rows(res, off, r0, r1)
+        oracle.lcs_pairs(res, off, pa, pb)
         dt = time.perf_counter() - t0
-        cells = float(sum(lens[i] * prefix[i] for i in range(r0, r1)))
+        cells = float((lens[pa].astype(np.float64) * lens[pb]).sum())
         if s >= args.warmup:
             vals.append(cells / dt / 1e9)
             tot_cells += cells
@@ -215,10 +232,10 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "k": k, "cells": cells_all,
                    "pairs": pairs_all,
-                   "sample_per_step": "DP LCS of %d rows against all earlier sequences" % rows},
+                   "sample_per_step": "DP LCS of %d seeded uniform random pairs" % n},
         "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": "per step: DP LCS of %d trailing rows of the family" % rows},
+                         "sample": "per step: DP LCS of %d seeded uniform random pairs of the family" % n},
         "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -681,7 +698,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-rows", type=int, default=12)
+    ap.add_argument("--ref-seconds", type=float, default=2.0,
+                    help="--impl reference: host seconds of oracle work per step")
     ap.add_argument("--update-path", type=int, default=0, choices=[0, 1, 2],
                     help="row-update kernel: 0 automatic, 1 cluster shared memory, 2 global memory "
                          "(profiling; the default picks by family size)")

@@ -52,7 +52,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
   // which row-update kernel, and its cluster size
   int path = g_update_path, cl = 0;
   if (path != 2) {
-    cl = smem_cluster_for(k, g_force_cluster);
+    cl = g_force_cluster ? smem_cluster_for(k, g_force_cluster) : smem_cluster_latency(k);
     if (cl > max_cluster_global()) cl = 0;
     if (cl == 0 && path == 1) return FAMSA_EINVAL;
     path = cl ? 1 : 2;

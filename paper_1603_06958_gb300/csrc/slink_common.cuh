@@ -267,6 +267,7 @@ cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int
                                 int32_t r1, int cl, cudaStream_t st);
 int max_cluster_global();
 int smem_cluster_for(int32_t k, int force);
+int smem_cluster_latency(int32_t k);
 cudaError_t launch_slink_smem(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
                               int32_t r1, int cl, int32_t k, bool narrow, cudaStream_t st);
 cudaError_t widen_keys(uint64_t *key, int32_t n, cudaStream_t st);

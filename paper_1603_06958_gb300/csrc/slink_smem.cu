@@ -718,6 +718,21 @@ int smem_cluster_for(int32_t k, int force) {
   return 0;
 }
 
+// Cluster size for one family on its own (latency): about 512 positions per
+// CTA or fewer (measured on the plain recipe: k = 1,000 is fastest on 2 CTAs,
+// 3,000 on 8, 6,000 and up on 16), never below the smallest that fits.
+// Batches keep the smallest cluster that fits, which costs the fewest
+// SM-seconds when many families share the GPU.
+int smem_cluster_latency(int32_t k) {
+  const int fit = smem_cluster_for(k, 0);
+  if (fit == 0) return 0;
+  int c = 1;
+  while (c < 16 && (int64_t)c * 512 < k) c *= 2;
+  c = c > fit ? c : fit;
+  // the wider cluster must fit too (it always does when a narrower one fits: P shrinks)
+  return smem_cluster_for(k, c) == c ? c : fit;
+}
+
 // The kernel's dynamic shared-memory cap and non-portable cluster permission
 // are set once, to the device maxima: a per-launch value could be lowered by
 // a concurrent caller between its setting and another caller's launch.
