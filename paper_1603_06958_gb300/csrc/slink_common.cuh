@@ -163,7 +163,6 @@ struct SlinkState {
   const int32_t *slen;     // lengths in insertion order
 };
 
-constexpr int kSlinkThreads = 1024;
 constexpr int kMaxClusterCtas = 16;
 constexpr int kRunsSmem = 2048;  // natural-run merges keep up to this many run starts per side
 
