@@ -703,8 +703,8 @@ def main():
     ap.add_argument("--update-path", type=int, default=0, choices=[0, 1, 2],
                     help="row-update kernel: 0 automatic, 1 cluster shared memory, 2 global memory "
                          "(profiling; the default picks by family size)")
-    ap.add_argument("--global-variant", type=int, default=0, choices=[0, 1],
-                    help="global-memory row update: 0 = 1,024 threads a CTA, 1 = 512")
+    ap.add_argument("--global-variant", type=int, default=-1, choices=[-1, 0, 1],
+                    help="global-memory row update: -1 by size (default), 0 = 1,024 threads a CTA, 1 = 512")
     ap.add_argument("--no-plain", action="store_true",
                     help="batch512: skip timing the one-family-at-a-time comparator")
     ap.add_argument("--int-peaks", action="store_true",

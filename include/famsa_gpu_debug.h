@@ -69,8 +69,9 @@ int famsa_debug_tpp_rows(int w);
  * so far, but keeps their choices until famsa_debug_set_tpp_rows resets them). */
 int famsa_debug_set_autotune(int on);
 
-/* Threads a CTA of the global-memory row-update kernel: 0 (default) 1,024,
- * 1 512.  Results are identical.  EINVAL outside 0..1. */
+/* Threads a CTA of the global-memory row-update kernel: -1 (default) by the
+ * row block's size (512 below 100,000 points, else 1,024), 0 1,024, 1 512.
+ * Results are identical.  EINVAL outside -1..1. */
 int famsa_debug_set_global_variant(int v);
 
 /* Thread-instructions per second of one integer instruction kind run as

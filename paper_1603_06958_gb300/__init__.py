@@ -536,7 +536,7 @@ def debug_set_autotune(on: bool):
 
 
 def debug_set_global_variant(v: int):
-    """Global-memory row update: 0 = 1,024 threads a CTA, 1 = 512."""
+    """Global-memory row update: -1 = by size (default), 0 = 1,024 threads a CTA, 1 = 512."""
     _check(load().famsa_debug_set_global_variant(int(v)), "famsa_debug_set_global_variant")
 
 
