@@ -402,11 +402,16 @@ static KParams batch_params(const Batch *b, uint16_t *rowbuf) {
 // ---- the autotuner: rows per thread-per-pair tile, per kernel width.  The
 // first batch with enough rows of a width times each allowed R on the same
 // sample of its rows (identical work) and keeps the fastest for the process
-// (the single-family launch planner uses it too).
+// (the single-family launch planner uses it too).  The sample is sized by
+// work, about 4e9 word steps (1.5 ms at the kernel's rate), so that every R
+// fills the GPU many times over: a sample of a few hundred CTAs favours the
+// smallest R only because it makes more of them.  Another R replaces the
+// default only when it is at least 2% faster.
 static std::mutex g_tune_mu;
 static bool g_tuned[kTppMaxW + 1] = {false};
 static std::atomic<int> g_autotune{1};
-constexpr size_t kTuneMinRows = 64, kTuneSampleRows = 1024;
+constexpr size_t kTuneMinRows = 64;
+constexpr double kTuneWordSteps = 4e9, kTuneMargin = 0.98;
 
 static cudaError_t time_rows(const Batch *b, uint16_t *rowbuf, const std::vector<BRow> &rows, size_t count,
                              int W, int R, const std::vector<int64_t> &h_peq_off,
@@ -461,20 +466,33 @@ static cudaError_t autotune_rows(Batch *b, uint16_t *rowbuf, const std::vector<B
                                  const std::vector<int64_t> &ld, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const auto t0 = std::chrono::steady_clock::now();
+  std::vector<int64_t> len_pre(b->Kpad + 1, 0);  // residues before each sorted position
+  for (int64_t s = 0; s < b->Kpad; ++s) len_pre[s + 1] = len_pre[s] + b->h_slen[s];
   for (size_t bk = 0; bk < buckets.size(); ++bk) {
     const Bucket &B = buckets[bk];
     const auto &rows = rows_by_bucket[bk];
     if (B.wpp || g_tuned[B.kw] || rows.size() < kTuneMinRows) continue;
-    const size_t count = std::min(rows.size(), kTuneSampleRows);
-    int best_R = tpp_default_rows(B.kw);
+    // rows in bucket order until the sample holds kTuneWordSteps (a row of W
+    // words takes W word steps per residue of the columns before it)
+    size_t count = 0;
+    double steps = 0.0;
+    while (count < rows.size() && steps < kTuneWordSteps) {
+      const BRow &r = rows[count];
+      steps += (double)B.kw * (double)(len_pre[r.rid] - len_pre[b->S[r.f]]);
+      ++count;
+    }
+    const int R0 = tpp_default_rows(B.kw);
+    int best_R = R0;
     float best_ms = 0.f;
-    bool any = false;
+    cudaError_t e = time_rows(b, rowbuf, rows, count, B.kw, R0, h_peq_off, rb_off, ld, st, &best_ms);
+    if (e != cudaSuccess) return e;
+    const float bar = best_ms * (float)kTuneMargin;
     for (int R : {1, 2, 4}) {
-      if (!tpp_rows_allowed(B.kw, R)) continue;
+      if (R == R0 || !tpp_rows_allowed(B.kw, R)) continue;
       float ms = 0.f;
-      const cudaError_t e = time_rows(b, rowbuf, rows, count, B.kw, R, h_peq_off, rb_off, ld, st, &ms);
+      e = time_rows(b, rowbuf, rows, count, B.kw, R, h_peq_off, rb_off, ld, st, &ms);
       if (e != cudaSuccess) return e;
-      if (!any || ms < best_ms) { best_ms = ms; best_R = R; any = true; }
+      if (ms < bar && ms < best_ms) { best_ms = ms; best_R = R; }
     }
     set_tpp_rows(B.kw, best_R);
     g_tuned[B.kw] = true;
