@@ -80,6 +80,13 @@ int famsa_debug_set_global_variant(int v);
  * and FMA pipes for the LCS roofline.  Allocates a small output buffer. */
 int famsa_debug_int_pipe_rate(int kind, double *inst_per_s);
 
+/* The row update's exact order code of the distance num / den (den in
+ * 1..32767, num < 2^32): floor(num * 2^30 / den), and back from a code to the
+ * distance as a reduced fraction.  Host-only arithmetic, no GPU needed;
+ * FAMSA_EINVAL for a den out of range or a null pointer. */
+int famsa_debug_order_code(uint32_t num, uint32_t den, uint64_t *code);
+int famsa_debug_code_fraction(uint64_t code, uint64_t *num, uint32_t *den);
+
 #ifdef __cplusplus
 }
 #endif

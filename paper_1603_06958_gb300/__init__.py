@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
             "famsa_debug_int_pipe_rate": ([ctypes.c_int, _P], ctypes.c_int),
             "famsa_debug_set_global_variant": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_order_code": ([ctypes.c_uint32, ctypes.c_uint32, _P], ctypes.c_int),
+            "famsa_debug_code_fraction": ([ctypes.c_uint64, _P, _P], ctypes.c_int),
             "famsa_debug_set_tpp_rows": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "famsa_debug_tpp_rows": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_autotune": ([ctypes.c_int], ctypes.c_int),
@@ -538,6 +540,21 @@ def debug_set_autotune(on: bool):
 def debug_set_global_variant(v: int):
     """Global-memory row update: -1 = by size (default), 0 = 1,024 threads a CTA, 1 = 512."""
     _check(load().famsa_debug_set_global_variant(int(v)), "famsa_debug_set_global_variant")
+
+
+def debug_order_code(num: int, den: int) -> int:
+    """The row update's exact order code of the distance num / den (host arithmetic)."""
+    out = ctypes.c_uint64()
+    _check(load().famsa_debug_order_code(int(num), int(den), ctypes.byref(out)), "famsa_debug_order_code")
+    return int(out.value)
+
+
+def debug_code_fraction(code: int) -> tuple:
+    """The reduced fraction (num, den) an order code came from (host arithmetic)."""
+    num, den = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(load().famsa_debug_code_fraction(int(code), ctypes.byref(num), ctypes.byref(den)),
+           "famsa_debug_code_fraction")
+    return int(num.value), int(den.value)
 
 
 def debug_set_cluster(ctas: int):

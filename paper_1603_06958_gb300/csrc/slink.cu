@@ -58,8 +58,8 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     path = cl ? 1 : 2;
   }
   if (path == 2) cl = g_force_cluster ? g_force_cluster : max_cluster_global();
-  // the shared-memory kernel packs keys as (num << 32) | den when every
-  // indel^2 fits in 32 bits (all lengths <= 32767)
+  // the shared-memory kernel compares exact order codes floor(num * 2^30 / den)
+  // when every indel^2 fits in 32 bits and every LCS in 15 (all lengths <= 32767)
   const bool narrow = path == 1 && f->max_len <= 32767;
 
   int prio_lo = 0, prio_hi = 0;
@@ -336,6 +336,18 @@ extern "C" int famsa_debug_sub_kcycles(const famsa_family *fh, int64_t *out16) {
 extern "C" int famsa_debug_set_update_path(int path) {
   if (path < 0 || path > 2) return FAMSA_EINVAL;
   famsa::g_update_path = path;
+  return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_order_code(uint32_t num, uint32_t den, uint64_t *code) {
+  if (!code || den == 0 || den > 32767) return FAMSA_EINVAL;
+  *code = famsa::order_code(num, den);
+  return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_code_fraction(uint64_t code, uint64_t *num, uint32_t *den) {
+  if (!num || !den) return FAMSA_EINVAL;
+  famsa::code_fraction(code, num, den);
   return FAMSA_OK;
 }
 

@@ -34,9 +34,62 @@ __device__ __forceinline__ uint64_t make_key(uint32_t L, uint32_t la, uint32_t l
   return ((indel * indel) << 16) | L;
 }
 
+// Exact order codes.  For a distance num / den with num < 2^32 and
+// 1 <= den <= 32767, code = floor(num * 2^30 / den) is strictly increasing in
+// the value: two different values differ by at least 1 / (den_a * den_b) >
+// 2^-30 (32767^2 < 2^30), so their scaled floors differ, and equal values get
+// equal codes.  Comparing codes is one 64-bit integer compare instead of two
+// multiplies.  The quotient is taken in three 15-bit digits after the integer
+// part, each a 32-bit division.
+__host__ __device__ __forceinline__ uint64_t order_code(uint32_t num, uint32_t den) {
+  const uint32_t q0 = num / den, r0 = num - q0 * den;
+  const uint32_t t1 = r0 << 15, q1 = t1 / den, r1 = t1 - q1 * den;
+  const uint32_t q2 = (r1 << 15) / den;
+  return ((uint64_t)q0 << 30) | ((uint64_t)q1 << 15) | q2;
+}
+
+// The distance an order code came from, as a reduced fraction p / q.  At most
+// one fraction with a denominator <= 32767 lies in [code, code + 1) / 2^30
+// (interval shorter than their spacing), so it is the fraction of smallest
+// denominator there: the continued-fraction descent of the Stern-Brocot tree
+// finds it.  y is tracked as x = (P1 y + P0) / (Q1 y + Q0) over intervals
+// [lo, hi) of y, each step peeling off the integer part and inverting.
+__host__ __device__ inline void code_fraction(uint64_t code, uint64_t *p, uint32_t *q) {
+  const uint64_t whole = code >> 30;
+  const uint32_t a = (uint32_t)(code & ((1u << 30) - 1));
+  if (a == 0) {
+    *p = whole;
+    *q = 1;
+    return;
+  }
+  // y in [ln/ld, hn/hd) with closedness flags; hd == 0 means +infinity
+  uint32_t ln = a, ld = 1u << 30, hn = a + 1, hd = 1u << 30;
+  bool lc = true, hc = false;
+  uint64_t P1 = 1, P0 = 0, Q1 = 0, Q0 = 1, y = 0;
+  for (int it = 0; it < 64; ++it) {
+    const uint32_t f = ln / ld, rem = ln - f * ld;
+    if (rem == 0 && lc) { y = f; break; }
+    const uint64_t g = (uint64_t)f + 1;  // the smallest integer above lo
+    if (hd == 0 || g * hd < hn || (g * hd == hn && hc)) { y = g; break; }
+    // no integer inside: y = f + 1/z, z in (1/(hi - f), 1/(lo - f)) with the ends swapped
+    const uint32_t nln = hd, nld = hn - f * hd;
+    const bool nlc = hc;
+    uint32_t nhn = 1, nhd = 0;
+    bool nhc = false;
+    if (rem != 0) { nhn = ld; nhd = rem; nhc = lc; }
+    uint64_t t = P1 * f + P0; P0 = P1; P1 = t;
+    t = Q1 * f + Q0; Q0 = Q1; Q1 = t;
+    ln = nln; ld = nld; lc = nlc; hn = nhn; hd = nhd; hc = nhc;
+  }
+  const uint64_t r = P1 * y + P0, s = Q1 * y + Q0;
+  *p = whole * s + r;
+  *q = (uint32_t)s;
+}
+
 // Two packings of the same exact key.  Wide: (num << 16) | den, any length
-// up to 65535.  Narrow: (num << 32) | den, when every length is <= 32767 so
-// that num = indel^2 < 2^32; a comparison is then two 32x32->64 multiplies.
+// up to 65535, compared by cross multiplication.  Narrow: the order code
+// above, when every length is <= 32767 so that num = indel^2 < 2^32 and
+// den = LCS <= 32767; +inf (LCS 0) is all ones.
 struct KeysWide {
   static constexpr uint64_t kInf = 1ull << 16;
   static constexpr uint64_t kZero = 1ull;
@@ -47,18 +100,22 @@ struct KeysWide {
   __device__ __forceinline__ static uint64_t wide(uint64_t k) { return k; }
 };
 struct KeysNarrow {
-  static constexpr uint64_t kInf = 1ull << 32;
-  static constexpr uint64_t kZero = 1ull;
-  __device__ __forceinline__ static bool lt(uint64_t a, uint64_t b) {
-    return (uint64_t)(uint32_t)(a >> 32) * (uint32_t)b < (uint64_t)(uint32_t)(b >> 32) * (uint32_t)a;
-  }
+  static constexpr uint64_t kInf = ~0ull;
+  static constexpr uint64_t kZero = 0ull;
+  __device__ __forceinline__ static bool lt(uint64_t a, uint64_t b) { return a < b; }
   __device__ __forceinline__ static uint64_t make(uint32_t L, uint32_t la, uint32_t lb) {
     if (L == 0) return kInf;
     const uint32_t indel = la + lb - 2 * L;
-    return ((uint64_t)(indel * indel) << 32) | L;
+    return order_code(indel * indel, L);
   }
-  __device__ __forceinline__ static uint64_t wide(uint64_t k) {
-    return ((k >> 32) << 16) | (k & 0xffffffffull);
+  // the same distance as a wide key, reduced (finalisation reduces every
+  // fraction it reports, so reduced and unreduced keys give the same output)
+  __host__ __device__ static uint64_t wide(uint64_t k) {
+    if (k == kInf) return KeysWide::kInf;
+    uint64_t p;
+    uint32_t q;
+    code_fraction(k, &p, &q);
+    return (p << 16) | q;
   }
 };
 

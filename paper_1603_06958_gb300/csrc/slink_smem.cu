@@ -16,9 +16,10 @@
 // run plus, for every other run, the number of that run's elements that go
 // before it: a search over every 16th value of D held locally, then one
 // window of at most 15 values read through DSMEM at once), two more barriers.  Runs beyond the
-// local capacity fall back to pairwise merges in global memory.  Keys are
-// compared by cross multiplication: packed as (indel^2 << 32) | LCS when every
-// length is at most 32767, else (indel^2 << 16) | LCS.
+// local capacity fall back to pairwise merges in global memory.  When every
+// length is at most 32767 a key is the exact order code floor(indel^2 * 2^30 /
+// LCS), compared as a plain integer; else it is (indel^2 << 16) | LCS,
+// compared by cross multiplication.
 #include <mutex>
 
 #include "slink_merge.cuh"
