@@ -654,7 +654,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     in.pi1 = S.pi[1];
     in.lam1 = S.lam[1];
     in.len0 = b->h_slen[b->S[f]];
-    in.inf = (smem && narrow) ? inf_narrow : inf_wide;  // the global-memory kernel keeps wide keys
+    in.inf = narrow ? inf_narrow : inf_wide;
     inits.push_back(in);
     if (smem) {
       const int ci = __builtin_ctz(cl);
@@ -692,7 +692,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     FB.hden = b->d_hden + om;
     FB.sizes = b->d_sizes + om;
     const int bk = k & 1;
-    fins.push_back(FinJob{f, k, smem && narrow, S.ord[bk], S.gap[bk], S.lam[bk], FB});
+    fins.push_back(FinJob{f, k, narrow, S.ord[bk], S.gap[bk], S.lam[bk], FB});
   }
   if (A.err != cudaSuccess) { err = A.err; goto fail; }
   BCK(upload_vec(A, inits, &d_init, st));
@@ -746,7 +746,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       }
       for (auto &g : global_fams) {
         if (e != cudaSuccess) break;
-        e = launch_slink_global(g.S, rowbuf + g.off, g.ld, 1, g.k, max_cl, b->cap);
+        e = launch_slink_global(g.S, rowbuf + g.off, g.ld, 1, g.k, max_cl, narrow, b->cap);
         ++launches;
       }
       // finalisation, spread over side streams

@@ -58,9 +58,9 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     path = cl ? 1 : 2;
   }
   if (path == 2) cl = g_force_cluster ? g_force_cluster : max_cluster_global();
-  // the shared-memory kernel compares exact order codes floor(num * 2^30 / den)
+  // both row-update kernels compare exact order codes floor(num * 2^30 / den)
   // when every indel^2 fits in 32 bits and every LCS in 15 (all lengths <= 32767)
-  const bool narrow = path == 1 && f->max_len <= 32767;
+  const bool narrow = f->max_len <= 32767;
 
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
@@ -201,7 +201,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       CKE(cudaStreamWaitEvent(sB, lcs_done[buf], 0));
       CKE(timing_event(sB));
       if (path == 1) CKE(launch_slink_smem(S, rowbuf[buf], ld, r0, r1, cl, k, narrow, sB));
-      else CKE(launch_slink_global(S, rowbuf[buf], ld, r0, r1, cl, sB));
+      else CKE(launch_slink_global(S, rowbuf[buf], ld, r0, r1, cl, narrow, sB));
       ++launches;
       CKE(timing_event(sB));
       CKE(cudaEventRecord(upd_done[buf], sB));

@@ -150,6 +150,10 @@ __device__ __forceinline__ Clamp shfl_clamp_idx(const Clamp &c, int src) {
   return Clamp{__shfl_sync(0xffffffffu, c.lo, src), __shfl_sync(0xffffffffu, c.hi, src)};
 }
 
+// The first shuffle distance of a tree reduction over the first n lanes (the
+// others hold the identity): the largest power of two below n, 0 for n <= 1.
+__device__ __forceinline__ int red_top(int n) { return n <= 1 ? 0 : 1 << (31 - __clz(n - 1)); }
+
 // Block-level exclusive scans of clamps, forward (thread order) and backward
 // (reverse thread order) at once.  sw needs 4*32+2 entries.  Returns the
 // thread's exclusive prefixes and the block totals.
@@ -175,8 +179,7 @@ __device__ __forceinline__ void block_scan2(Clamp vf, Clamp vb, Clamp *pf, Clamp
   if (warp == 0) {
     Clamp wf = lane < nw ? sw[lane] : identity_clamp<K>();
     Clamp wb = lane < nw ? sw[32 + lane] : identity_clamp<K>();
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (int d = 1; d < nw; d <<= 1) {  // lanes >= nw hold the identity
       Clamp yf = shfl_clamp_up(wf, d);
       Clamp yb = shfl_clamp_down(wb, d);
       if (lane >= d) wf = compose<K>(yf, wf);
@@ -320,7 +323,7 @@ size_t fin_levels(int32_t k);
 cudaError_t launch_finalize(const int32_t *ord, const uint64_t *gap, const int32_t *perm, int32_t k,
                             FinBufs &B, cudaStream_t st, int64_t *launches);
 cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
-                                int32_t r1, int cl, cudaStream_t st);
+                                int32_t r1, int cl, bool narrow, cudaStream_t st);
 int max_cluster_global();
 int smem_cluster_for(int32_t k, int force);
 int smem_cluster_latency(int32_t k);

@@ -32,7 +32,7 @@ struct GBest {
 // consecutive positions of the tile, and one warp scan over the 32 lane
 // totals joins them.  Shared arrays are padded one slot per lane block so
 // that the lanes' strided accesses do not collide in one bank.
-template <int kThreads, int kE>
+template <class K, int kThreads, int kE>
 __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   constexpr int kWarps = kThreads / 32;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
   __shared__ int32_t sRunsA[kRunsSmem], sRunsB[kRunsSmem];
   const SlinkState &S = a.s;
   uint64_t *ctl = S.ctl;
-  constexpr uint64_t INF = kKeyInf;
+  constexpr uint64_t INF = K::kInf;
 
   // cycles of one thread per phase (A distances + summaries, B scans + pointer
   // update, C re-layout, D run merges), for the counters of famsa_last_stats
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
     // ---- phase A: distances, warp totals of both scans (L in position order, R reversed)
     const int32_t wpos_b = row_b << 5, wpos_e = min(row_e << 5, m);
     {
-      Clamp wL = identity_clamp(), wR = identity_clamp();
+      Clamp wL = identity_clamp<K>(), wR = identity_clamp<K>();
       for (int32_t tb = wpos_b; tb < wpos_e; tb += kTile) {
         const int32_t te = min(tb + kTile, wpos_e);
 #pragma unroll
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
           }
         }
         __syncwarp();
-        Clamp tL = identity_clamp(), tR = identity_clamp();
+        Clamp tL = identity_clamp<K>(), tR = identity_clamp<K>();
         {
           uint16_t rv[kE];
 #pragma unroll
@@ -123,10 +123,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
           for (int i = 0; i < kE; ++i) {
             const int32_t k = lane * kE + i;
             if (tb + k < te) {
-              const uint64_t d = make_key(rv[i], (uint32_t)sI1[sidx(k)], ln);
+              const uint64_t d = K::make(rv[i], (uint32_t)sI1[sidx(k)], ln);
               sD[sidx(k)] = d;
-              tL = compose(tL, Clamp{sG[gidx(k)], d});
-              tR = compose(Clamp{sG[gidx(k + 1)], d}, tR);
+              tL = compose<K>(tL, Clamp{sG[gidx(k)], d});
+              tR = compose<K>(Clamp{sG[gidx(k + 1)], d}, tR);
             }
           }
         }
@@ -140,12 +140,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
         for (int s = 1; s < 32; s <<= 1) {
           const Clamp yL = shfl_clamp_down(tL, s), yR = shfl_clamp_down(tR, s);
           if (lane + s < 32) {
-            tL = compose(tL, yL);
-            tR = compose(yR, tR);
+            tL = compose<K>(tL, yL);
+            tR = compose<K>(yR, tR);
           }
         }
-        wL = compose(wL, shfl_clamp_idx(tL, 0));
-        wR = compose(shfl_clamp_idx(tR, 0), wR);
+        wL = compose<K>(wL, shfl_clamp_idx(tL, 0));
+        wR = compose<K>(shfl_clamp_idx(tR, 0), wR);
         __syncwarp();
       }
       GSUB(0)
@@ -157,18 +157,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
       GSUB(1)
       if (warp == 0) {
         // exclusive prefixes of the warps (L from the left, R from the right) and CTA totals
-        Clamp vL = lane < kWarps ? sWL[lane] : identity_clamp();
-        Clamp vR = lane < kWarps ? sWR[lane] : identity_clamp();
+        Clamp vL = lane < kWarps ? sWL[lane] : identity_clamp<K>();
+        Clamp vR = lane < kWarps ? sWR[lane] : identity_clamp<K>();
         Clamp iL = vL, iR = vR;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
           const Clamp yL = shfl_clamp_up(iL, s), yR = shfl_clamp_down(iR, s);
-          if (lane >= s) iL = compose(yL, iL);
-          if (lane + s < 32) iR = compose(yR, iR);
+          if (lane >= s) iL = compose<K>(yL, iL);
+          if (lane + s < 32) iR = compose<K>(yR, iR);
         }
         Clamp eL = shfl_clamp_up(iL, 1), eR = shfl_clamp_down(iR, 1);
-        if (lane == 0) eL = identity_clamp();
-        if (lane == 31) eR = identity_clamp();
+        if (lane == 0) eL = identity_clamp<K>();
+        if (lane == 31) eR = identity_clamp<K>();
         if (lane < kWarps) {
           sWL[lane] = eL;
           sWR[lane] = eR;
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
 
     // ---- phase B: finish the scans, D, pointer update, first minimum
     if (threadIdx.x == 0) {
-      Clamp cl = identity_clamp(), cr = identity_clamp();
-      for (int32_t c = 0; c < cta; ++c) cl = compose(cl, sAggL[c]);
-      for (int32_t c = ncta - 1; c > cta; --c) cr = compose(cr, sAggR[c]);
+      Clamp cl = identity_clamp<K>(), cr = identity_clamp<K>();
+      for (int32_t c = 0; c < cta; ++c) cl = compose<K>(cl, sAggL[c]);
+      for (int32_t c = ncta - 1; c > cta; --c) cr = compose<K>(cr, sAggR[c]);
       sCtaPre[0] = cl;
       sCtaPre[1] = cr;
     }
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
     int32_t bestpos = INT32_MAX;
     {
       // forward: Lf of every position, tile by tile
-      Clamp run = compose(sCtaPre[0], sWL[warp]);
+      Clamp run = compose<K>(sCtaPre[0], sWL[warp]);
       for (int32_t tb = wpos_b; tb < wpos_e; tb += kTile) {
         const int32_t te = min(tb + kTile, wpos_e);
 #pragma unroll
@@ -219,30 +219,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
           }
         }
         __syncwarp();
-        Clamp t = identity_clamp();
+        Clamp t = identity_clamp<K>();
 #pragma unroll
         for (int i = 0; i < kE; ++i) {
           const int32_t k = lane * kE + i;
-          if (tb + k < te) t = compose(t, Clamp{sG[gidx(k)], sD[sidx(k)]});
+          if (tb + k < te) t = compose<K>(t, Clamp{sG[gidx(k)], sD[sidx(k)]});
         }
         Clamp inc = t;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
           const Clamp y = shfl_clamp_up(inc, s);
-          if (lane >= s) inc = compose(y, inc);
+          if (lane >= s) inc = compose<K>(y, inc);
         }
         Clamp ex = shfl_clamp_up(inc, 1);
-        if (lane == 0) ex = identity_clamp();
-        uint64_t x = compose(run, ex).hi;
+        if (lane == 0) ex = identity_clamp<K>();
+        uint64_t x = compose<K>(run, ex).hi;
 #pragma unroll
         for (int i = 0; i < kE; ++i) {
           const int32_t k = lane * kE + i;
           if (tb + k < te) {
-            x = kmin(sD[sidx(k)], kmax(x, sG[gidx(k)]));
+            x = kmin_t<K>(sD[sidx(k)], kmax_t<K>(x, sG[gidx(k)]));
             sX[sidx(k)] = x;
           }
         }
-        run = compose(run, shfl_clamp_idx(inc, 31));
+        run = compose<K>(run, shfl_clamp_idx(inc, 31));
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < kE; ++j) {
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
       }
       // backward: Rf, D, the pointer update and the first minimum, tiles from the right
       GSUB(5)
-      run = compose(sCtaPre[1], sWR[warp]);
+      run = compose<K>(sCtaPre[1], sWR[warp]);
       const int32_t ntiles = (wpos_e - wpos_b + kTile - 1) / kTile;
       for (int32_t ti = ntiles - 1; ti >= 0; --ti) {
         const int32_t tb = wpos_b + ti * kTile;
@@ -277,37 +277,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
           }
         }
         __syncwarp();
-        Clamp t = identity_clamp();
+        Clamp t = identity_clamp<K>();
 #pragma unroll
         for (int i = kE - 1; i >= 0; --i) {
           const int32_t k = lane * kE + i;
-          if (tb + k < te) t = compose(t, Clamp{sG[gidx(k + 1)], sD[sidx(k)]});
+          if (tb + k < te) t = compose<K>(t, Clamp{sG[gidx(k + 1)], sD[sidx(k)]});
         }
         Clamp inc = t;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
           const Clamp y = shfl_clamp_down(inc, s);
-          if (lane + s < 32) inc = compose(y, inc);
+          if (lane + s < 32) inc = compose<K>(y, inc);
         }
         Clamp ex = shfl_clamp_down(inc, 1);
-        if (lane == 31) ex = identity_clamp();
-        uint64_t x = compose(run, ex).hi;
+        if (lane == 31) ex = identity_clamp<K>();
+        uint64_t x = compose<K>(run, ex).hi;
 #pragma unroll
         for (int i = kE - 1; i >= 0; --i) {
           const int32_t k = lane * kE + i;
           const int32_t p = tb + k;
           if (p < te) {
-            x = kmin(sD[sidx(k)], kmax(x, sG[gidx(k + 1)]));
-            const uint64_t Dq = kmin(sX[sidx(k)], x);
+            x = kmin_t<K>(sD[sidx(k)], kmax_t<K>(x, sG[gidx(k + 1)]));
+            const uint64_t Dq = kmin_t<K>(sX[sidx(k)], x);
             sX[sidx(k)] = Dq;
-            if (!klt(sL[sidx(k)], Dq)) {  // D <= lambda: the point's pointer moves to n
+            if (!K::lt(sL[sidx(k)], Dq)) {  // D <= lambda: the point's pointer moves to n
               sL[sidx(k)] = Dq;
               sI0[sidx(k)] = n;
             }
-            if (klt(Dq, best) || (!klt(best, Dq) && p < bestpos)) { best = Dq; bestpos = p; }
+            if (K::lt(Dq, best) || (!K::lt(best, Dq) && p < bestpos)) { best = Dq; bestpos = p; }
           }
         }
-        run = compose(run, shfl_clamp_idx(inc, 0));
+        run = compose<K>(run, shfl_clamp_idx(inc, 0));
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < kE; ++j) {
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
     for (int d = 16; d > 0; d >>= 1) {
       const uint64_t ob = __shfl_down_sync(0xffffffffu, best, d);
       const int32_t op = __shfl_down_sync(0xffffffffu, bestpos, d);
-      if (klt(ob, best) || (!klt(best, ob) && op < bestpos)) { best = ob; bestpos = op; }
+      if (K::lt(ob, best) || (!K::lt(best, ob) && op < bestpos)) { best = ob; bestpos = op; }
     }
     if (lane == 0) { sWBest[warp] = best; sWBestPos[warp] = bestpos; }
     __syncthreads();
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
       for (int d = 16; d > 0; d >>= 1) {
         const uint64_t ob = __shfl_down_sync(0xffffffffu, best, d);
         const int32_t op = __shfl_down_sync(0xffffffffu, bestpos, d);
-        if (klt(ob, best) || (!klt(best, ob) && op < bestpos)) { best = ob; bestpos = op; }
+        if (K::lt(ob, best) || (!K::lt(best, ob) && op < bestpos)) { best = ob; bestpos = op; }
       }
       GBest gb;
       gb.key = __shfl_sync(0xffffffffu, best, 0);
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
       for (int32_t c = 0; c < ncta; ++c) {
         const uint64_t v = sBest[c].key;
         const int32_t p = sBest[c].pos;
-        if (klt(v, b) || (!klt(b, v) && p < bp)) { b = v; bp = p; }
+        if (K::lt(v, b) || (!K::lt(b, v) && p < bp)) { b = v; bp = p; }
       }
       x0 = bp;
     }
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
         if (p + 1 < m) {
           const uint64_t Dn = S.D[p + 1];
           if (p + 1 == x0) ngap[p] = Dp;  // last of the left side, then n
-          else ngap[np] = kmin(kmax(Dp, Dn), gap[p]);
+          else ngap[np] = kmin_t<K>(kmax_t<K>(Dp, Dn), gap[p]);
         }
         if (p == x0) {
           nord[x0] = n;
@@ -389,11 +389,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
           npi[x0] = n;
           ngap[x0] = Dp;  // n, then old position x0
         }
-        if (p >= 1 && p < x0 && klt(S.D[p - 1], Dp)) {
+        if (p >= 1 && p < x0 && K::lt(S.D[p - 1], Dp)) {
           const uint64_t at = atomicAdd((unsigned long long *)&ctl[kCtlCnt + 2 * slot], 1ull);
           S.runsA[at] = p;
         }
-        if (p > x0 && klt(Dp, S.D[p - 1])) {
+        if (p > x0 && K::lt(Dp, S.D[p - 1])) {
           const uint64_t at = atomicAdd((unsigned long long *)&ctl[kCtlCnt + 2 * slot + 1], 1ull);
           S.runsB[at] = p;
         }
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
       }
       if (tid == 0) ctl[kCtlStats] += 1;
       cluster.sync();
-      const int src = merge_rounds(S, cluster, m, x0, natural, sRunsA, nA, sRunsB, nB, cb, ce, tid == 0);
+      const int src = merge_rounds<K>(S, cluster, m, x0, natural, sRunsA, nA, sRunsB, nB, cb, ce, tid == 0);
       for (int32_t p = cb; p < ce; ++p) {
         const int32_t np = p < x0 ? p : p + 1;
         nord[np] = S.mOrd[src][p];
@@ -446,14 +446,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_slink_global(GlobalArgs a) {
         if (p + 1 < m && p + 1 != x0) {
           const uint64_t Dn = S.mD[src][p + 1];
           const int32_t o = S.mOld[src][p], on = S.mOld[src][p + 1];
-          uint64_t g = kmax(Dp, Dn);
-          if (on == o + 1) g = kmin(g, gap[o]);
+          uint64_t g = kmax_t<K>(Dp, Dn);
+          if (on == o + 1) g = kmin_t<K>(g, gap[o]);
           ngap[np] = g;
         }
         if (p == x0) {
           nord[x0] = n;
           nlen[x0] = (int32_t)ln;
-          nlam[x0] = kKeyInf;
+          nlam[x0] = INF;
           npi[x0] = n;
         }
       }
@@ -483,22 +483,22 @@ constexpr size_t global_smem_bytes() {
   return (size_t)(T / 32) * (4 * 32 * (E + 1) + 1 + 32 * (E + 1)) * sizeof(uint64_t);
 }
 
-template <int T, int E>
+template <class K, int T, int E>
 static cudaError_t global_kernel_attributes() {
   static std::once_flag once;
   static cudaError_t result = cudaSuccess;
   std::call_once(once, [] {
-    cudaError_t e = cudaFuncSetAttribute(k_slink_global<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_slink_global<K, T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)global_smem_bytes<T, E>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slink_global<T, E>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slink_global<K, T, E>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     result = e;
   });
   return result;
 }
 
-template <int T, int E>
+template <class K, int T, int E>
 static cudaError_t launch_global_t(const GlobalArgs &args, int cl, cudaStream_t st) {
-  cudaError_t e = global_kernel_attributes<T, E>();
+  cudaError_t e = global_kernel_attributes<K, T, E>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl, 1, 1);
@@ -512,11 +512,11 @@ static cudaError_t launch_global_t(const GlobalArgs &args, int cl, cudaStream_t 
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_slink_global<T, E>, args);
+  return cudaLaunchKernelEx(&cfg, k_slink_global<K, T, E>, args);
 }
 
 cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
-                                int32_t r1, int cl, cudaStream_t st) {
+                                int32_t r1, int cl, bool narrow, cudaStream_t st) {
   GlobalArgs args;
   args.s = S;
   args.rowbuf = rowbuf;
@@ -524,13 +524,15 @@ cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int
   args.r0 = r0;
   args.r1 = r1;
   const int v = g_global_variant >= 0 ? g_global_variant : (r1 < 100000 ? 1 : 0);
-  return v == 1 ? launch_global_t<512, 8>(args, cl, st) : launch_global_t<1024, 4>(args, cl, st);
+  if (narrow)
+    return v == 1 ? launch_global_t<KeysNarrow, 512, 8>(args, cl, st) : launch_global_t<KeysNarrow, 1024, 4>(args, cl, st);
+  return v == 1 ? launch_global_t<KeysWide, 512, 8>(args, cl, st) : launch_global_t<KeysWide, 1024, 4>(args, cl, st);
 }
 
 int max_cluster_global() {
   static int cached = 0;
   if (cached) return cached;
-  if (global_kernel_attributes<1024, 4>() != cudaSuccess) {
+  if (global_kernel_attributes<KeysWide, 1024, 4>() != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -547,7 +549,7 @@ int max_cluster_global() {
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_slink_global<1024, 4>, &cfg) == cudaSuccess && n >= 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_slink_global<KeysWide, 1024, 4>, &cfg) == cudaSuccess && n >= 1) {
       cached = w;
       return w;
     }
