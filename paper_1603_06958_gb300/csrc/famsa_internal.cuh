@@ -22,6 +22,11 @@ constexpr int kGroup = 32;          // columns per group (one warp)
 constexpr int kChunk = 16;          // residues per interleaved chunk (one 16-byte load)
 constexpr int kTppMaxW = 32;        // thread-per-pair handles rows of up to 32 words
 constexpr int kStatsLen = 24;       // famsa_last_stats entries
+// Row blocks of 16-bit LCS values in flight between the LCS kernels and the
+// row update: the LCS may run this many blocks minus one ahead, so that it
+// fills the early blocks' slack (where the row update is the longer) and the
+// row update never waits on it later (where the LCS per block is the longer).
+constexpr int kRowBuffers = 4;
 
 // Peq layout (row side): for each sequence s and word w, 64 uint32:
 //   [0..32)  low 32 bits of the mask for symbols 0..31

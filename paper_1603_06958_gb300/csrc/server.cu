@@ -83,13 +83,13 @@ static int64_t tree_estimate(const std::vector<int64_t> &off, int32_t k, int64_t
   const int64_t groups = (k + 31) / 32;
   // residues, offsets, lengths/permutation, Peq planes, column layout
   *resident = sum + 8 * (int64_t)(k + 1) * 2 + 16 * (int64_t)k + words * 256 + sum + sum / 4 + 1024 * groups;
-  // tree build: two row blocks of 16-bit LCS, the row-update state, the finalisation tables
+  // tree build: the row blocks of 16-bit LCS, the row-update state, the finalisation tables
   int64_t B = std::min<int64_t>(std::max<int64_t>((int64_t)(1 << 26) / std::max(k, 1), 64), 2048);
   B = std::min<int64_t>(B, std::max(k - 1, 1));
   const int64_t ld = (k + 1) & ~1ll;
   int64_t lv = 1;
   while ((1ll << lv) <= k) ++lv;
-  return *resident + 2 * B * ld * 2 + (int64_t)k * 160 + (int64_t)k * (96 + 16 * lv) + (16 << 20);
+  return *resident + kRowBuffers * B * ld * 2 + (int64_t)k * 160 + (int64_t)k * (96 + 16 * lv) + (16 << 20);
 }
 
 static int64_t query_estimate(const std::vector<int64_t> &off, int32_t nq, int32_t k) {

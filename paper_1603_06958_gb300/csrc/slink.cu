@@ -65,8 +65,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   cudaStream_t sA = nullptr, sB = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_end = nullptr, lcs_done[2] = {nullptr, nullptr},
-              upd_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr, lcs_done[kRowBuffers] = {}, upd_done[kRowBuffers] = {};
   Scratch sc;
   sc.st = st;
   int64_t launches = 0, lcs_launches = 0;
@@ -90,7 +89,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
   CKE(cudaStreamCreateWithPriority(&sB, cudaStreamNonBlocking, prio_hi));
   CKE(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
   CKE(cudaEventCreateWithFlags(&ev_end, cudaEventDisableTiming));
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kRowBuffers; ++i) {
     CKE(cudaEventCreateWithFlags(&lcs_done[i], cudaEventDisableTiming));
     CKE(cudaEventCreateWithFlags(&upd_done[i], cudaEventDisableTiming));
   }
@@ -121,9 +120,8 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     int32_t B = (int32_t)std::min<int64_t>(std::max<int64_t>((int64_t)(1 << 26) / std::max(k, 1), 64), 2048);
     B = std::min(B, std::max(k - 1, 1));
     const int64_t ld = (k + 1) & ~1;  // even: rows start on 4-byte boundaries
-    uint16_t *rowbuf[2];
-    rowbuf[0] = sc.get<uint16_t>((size_t)B * ld);
-    rowbuf[1] = sc.get<uint16_t>((size_t)B * ld);
+    uint16_t *rowbuf[kRowBuffers];
+    for (int i = 0; i < kRowBuffers; ++i) rowbuf[i] = sc.get<uint16_t>((size_t)B * ld);
     std::vector<int32_t> h_iota(k), h_w(k);
     for (int32_t s = 0; s < k; ++s) { h_iota[s] = s; h_w[s] = (f->h_slen[s] + 63) / 64; }
     int32_t *d_iota = sc.get<int32_t>(k);
@@ -170,9 +168,9 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     int32_t blk = 0;
     for (int32_t r0 = 1; r0 < k; r0 += B, ++blk) {
       const int32_t r1 = std::min(r0 + B, k);
-      const int buf = blk & 1;
-      if (blk >= 2) CKE(cudaStreamWaitEvent(sA, upd_done[buf], 0));
-      if (g_serial && blk >= 1) CKE(cudaStreamWaitEvent(sA, upd_done[buf ^ 1], 0));
+      const int buf = blk % kRowBuffers;
+      if (blk >= kRowBuffers) CKE(cudaStreamWaitEvent(sA, upd_done[buf], 0));
+      if (g_serial && blk >= 1) CKE(cudaStreamWaitEvent(sA, upd_done[(blk - 1) % kRowBuffers], 0));
       LcsBatch b;
       b.peq = f->d_peq;
       b.colres = f->d_colres;
@@ -304,7 +302,7 @@ done:
   if (sB) cudaStreamDestroy(sB);
   if (ev_start) cudaEventDestroy(ev_start);
   if (ev_end) cudaEventDestroy(ev_end);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kRowBuffers; ++i) {
     if (lcs_done[i]) cudaEventDestroy(lcs_done[i]);
     if (upd_done[i]) cudaEventDestroy(upd_done[i]);
   }

@@ -198,7 +198,8 @@ __device__ __forceinline__ void block_scan2(Clamp vf, Clamp vb, Clamp *pf, Clamp
   *pb = compose<K>(sw[96 + warp], excb);
   *tf = sw[128];
   *tb = sw[129];
-  __syncthreads();
+  // no trailing barrier: the next call writes sw[0..64) before its first
+  // barrier and the result slots sw[64..130) only after it
 }
 
 // ----------------------------------------------------------------- state

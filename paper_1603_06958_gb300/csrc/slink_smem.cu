@@ -14,9 +14,10 @@
 // When a side is not monotone it is a few sorted runs: each element's place
 // in the stable merge of its side is found in one pass (its index in its own
 // run plus, for every other run, the number of that run's elements that go
-// before it: a search over every 16th value of D held locally, then one
-// window of at most 15 values read through DSMEM at once), two more barriers.  Runs beyond the
-// local capacity fall back to pairwise merges in global memory.  When every
+// before it: a search over every 16th value of D held locally, then a binary
+// search through DSMEM inside a window of at most 15 values), two more
+// barriers.  Runs beyond the local capacity fall back to pairwise merges in
+// global memory.  When every
 // length is at most 32767 a key is the exact order code floor(indel^2 * 2^30 /
 // LCS), compared as a plain integer; else it is (indel^2 << 16) | LCS,
 // compared by cross multiplication.
@@ -213,8 +214,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
         aL = sAggL[lane];
         aR = sAggR[lane];
       }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
+      for (int d = 1; d < ncta; d <<= 1) {  // lanes >= ncta hold the identity
         Clamp yf = shfl_clamp_up(aL, d);
         Clamp yb = shfl_clamp_down(aR, d);
         if (lane >= d) aL = compose<K>(yf, aL);
@@ -279,8 +279,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
       bestpos = lane < nw ? sRedPos[lane] : INT32_MAX;
       masc = lane < nw ? sRedA[lane] : INT32_MAX;
       mdesc = lane < nw ? sRedD[lane] : -1;
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
+      for (int d = red_top(nw); d > 0; d >>= 1) {
         const uint64_t ob = __shfl_down_sync(0xffffffffu, best, d);
         const int32_t op = __shfl_down_sync(0xffffffffu, bestpos, d);
         if (K::lt(ob, best) || (!K::lt(best, ob) && op < bestpos)) { best = ob; bestpos = op; }
@@ -322,8 +321,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
         if (K::lt(prevLast, f)) ma = min(ma, pb);
         if (K::lt(f, prevLast)) md = max(md, pb);
       }
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
+      for (int d = red_top(ncta); d > 0; d >>= 1) {
         const uint64_t ob = __shfl_down_sync(0xffffffffu, b, d);
         const int32_t op = __shfl_down_sync(0xffffffffu, bp, d);
         if (K::lt(ob, b) || (!K::lt(b, ob) && op < bp)) { b = ob; bp = op; }
@@ -511,7 +509,9 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
             // the boundary lies in [wlo, whi): after the last true sample, up to the first false one
             const int32_t wlo = lo > qa ? ((lo - 1) << sshift) + 1 : s0;
             const int32_t whi = lo <= qb ? (lo << sshift) : e0;
-            // binary search inside the window (fewer than 2^sshift positions) through DSMEM
+            // binary search inside the window (fewer than 2^sshift positions)
+            // through DSMEM: a few dependent loads measured faster than reading
+            // the whole window with independent loads
             int32_t wa = wlo, wb = whi;
             while (wa < wb) {
               const int32_t mid = (wa + wb) >> 1;
