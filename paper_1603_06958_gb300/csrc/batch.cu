@@ -738,16 +738,26 @@ static int batch_plan(Batch *b, cudaStream_t st) {
         e = cudaGetLastError();
         ++launches;
       }
-      for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
-        if (smem_args[ci].empty()) continue;
-        e = launch_slink_smem_batch(d_sargs[ci], (int32_t)smem_args[ci].size(), 1 << ci, smem_dyn[ci],
-                                    narrow, b->cap);
-        ++launches;
-      }
-      for (auto &g : global_fams) {
-        if (e != cudaSuccess) break;
-        e = launch_slink_global(g.S, rowbuf + g.off, g.ld, 1, g.k, max_cl, narrow, b->cap);
-        ++launches;
+      // the launches of each cluster size, and the global-memory families, run
+      // side by side (one branch of the graph each): a launch's tail of large
+      // families no longer holds back the next cluster size
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->cap);
+      for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
+        if (ci < 5 ? smem_args[ci].empty() : global_fams.empty()) continue;
+        cudaStream_t s = b->side[ci];
+        e = cudaStreamWaitEvent(s, b->ev[0], 0);
+        if (e == cudaSuccess && ci < 5) {
+          e = launch_slink_smem_batch(d_sargs[ci], (int32_t)smem_args[ci].size(), 1 << ci, smem_dyn[ci],
+                                      narrow, s);
+          ++launches;
+        }
+        for (size_t gi = 0; ci == 5 && gi < global_fams.size() && e == cudaSuccess; ++gi) {
+          const GlobalFam &g = global_fams[gi];
+          e = launch_slink_global(g.S, rowbuf + g.off, g.ld, 1, g.k, max_cl, narrow, s);
+          ++launches;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev[1 + ci], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev[1 + ci], 0);
       }
       // finalisation, spread over side streams
       if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[2], b->cap, cudaEventRecordExternal);
