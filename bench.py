@@ -304,15 +304,18 @@ def run_batch(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ms, graph_ms, stats = [], [], []
+    ms, graph_ms, pack_ms, stats = [], [], [], []
     for _ in range(args.steps):
         flush.zero_()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, ep, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         e0.record()
-        b, _ = step()
+        b = fg.batch_pack(dres, doff, fo)
+        ep.record()
+        fg.batch_tree(b, device=True)
         e1.record()
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+        pack_ms.append(e0.elapsed_time(ep))
         stats.append(b.stats())
         # the same graph again: the steady state of a resident batch
         flush.zero_()
@@ -385,7 +388,9 @@ def run_batch(args, rank, world, local_rank):
                    "breakdown_ms": {"lcs_kernels": lcs_ms,
                                     "row_update_kernels": float(np.mean([s["update_ns"] for s in stats])) / 1e6,
                                     "finalise": float(np.mean([s["finalize_ns"] for s in stats])) / 1e6,
-                                    "graph_only": float(np.mean(graph_ms))},
+                                    "graph_only": float(np.mean(graph_ms)),
+                                    "pack": float(np.mean(pack_ms)),
+                                    "plan_and_capture": ms_step - float(np.mean(pack_ms)) - float(np.mean(graph_ms))},
                    "graph_only_gcups": cells / (float(np.mean(graph_ms)) * 1e-3) / 1e9,
                    "plain_ms": plain_ms,
                    "plain_gcups": (cells / (plain_ms * 1e-3) / 1e9) if plain_ms else None,
