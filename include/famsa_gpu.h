@@ -63,6 +63,22 @@ const char *famsa_strerror(int status);
 int famsa_version(void);
 
 /*
+ * famsa_encode_ascii -- map protein letters to the residue codes every other
+ * call takes (host only, no CUDA).  The paper's alphabet is the twenty amino
+ * acids plus a few special symbols ("Pairwise similarities calculation"); the
+ * reading here is codes 0-19 = A C D E F G H I K L M N P Q R S T V W Y and
+ * 20 = B, 21 = Z, 22 = X, 23 = U, 24 = O.  Lowercase letters map like
+ * uppercase; any other byte (gap '-', stop '*', digits, J, whitespace) is an
+ * error, never a silent substitution.
+ *   text      n bytes (host).
+ *   codes     n bytes (host, caller-owned), written only on success.
+ *   bad_pos   optional: the index of the first rejected byte, or -1.
+ * Returns FAMSA_OK, or FAMSA_EINVAL for a NULL pointer, n < 0 or a rejected
+ * byte.
+ */
+int famsa_encode_ascii(const char *text, int64_t n, uint8_t *codes, int64_t *bad_pos);
+
+/*
  * famsa_pack_peq -- validate a family, copy it to the device and build its
  * match-bitmask tables ("Pairwise similarities calculation": the LCS is
  * computed bit-parallel, w = 64 DP cells per machine word, which needs for

@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
         sig = {
             "famsa_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "famsa_version": ([], ctypes.c_int),
+            "famsa_encode_ascii": ([ctypes.c_char_p, ctypes.c_int64, _P, _P], ctypes.c_int),
             "famsa_pack_peq": ([_P, _P, i32, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
             "famsa_family_size": ([_P], i32),
             "famsa_lcs_allpairs": ([_P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -242,6 +243,30 @@ def famsa_lcs_rows(fam: Family, row_begin: int, row_end: int, out=None, device: 
 
 
 lcs_rows = famsa_lcs_rows
+
+
+def famsa_encode_ascii(text) -> np.ndarray:
+    """Protein letters (str or bytes, either case) -> residue codes 0..24; any
+    other byte raises FamsaError naming its position."""
+    data = text.encode("ascii", "strict") if isinstance(text, str) else bytes(text)
+    out = np.empty(len(data), dtype=np.uint8)
+    bad = ctypes.c_int64(-1)
+    st = load().famsa_encode_ascii(data, len(data), out.ctypes.data, ctypes.byref(bad))
+    if st != FAMSA_OK:
+        raise FamsaError(st, "famsa_encode_ascii (byte %d)" % bad.value)
+    return out
+
+
+encode_ascii = famsa_encode_ascii
+
+
+def merge_similarity(tree: dict) -> np.ndarray:
+    """The merge heights as the paper's similarity LCS / indel^2 (= h_den / h_num),
+    a float64 convenience beside the exact fractions; +inf for height 0."""
+    num = np.asarray(tree["h_num"], dtype=np.float64)
+    den = np.asarray(tree["h_den"], dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        return np.where(num == 0, np.inf, den / np.where(num == 0, 1, num))
 
 
 def famsa_slink_tree(fam: Family, device: bool = False, stream=None) -> dict:

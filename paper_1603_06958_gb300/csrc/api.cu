@@ -66,6 +66,26 @@ const char *famsa_strerror(int status) {
 
 int famsa_version(void) { return 10000; }
 
+int famsa_encode_ascii(const char *text, int64_t n, uint8_t *codes, int64_t *bad_pos) {
+  if (bad_pos) *bad_pos = -1;
+  if (!text || !codes || n < 0) return FAMSA_EINVAL;
+  static const char kAlphabet[] = "ACDEFGHIKLMNPQRSTVWYBZXUO";  // code = index
+  int8_t table[256];
+  for (int c = 0; c < 256; ++c) table[c] = -1;
+  for (int i = 0; i < kCodes; ++i) {
+    table[(unsigned char)kAlphabet[i]] = (int8_t)i;
+    table[(unsigned char)(kAlphabet[i] - 'A' + 'a')] = (int8_t)i;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (table[(unsigned char)text[i]] < 0) {
+      if (bad_pos) *bad_pos = i;
+      return FAMSA_EINVAL;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) codes[i] = (uint8_t)table[(unsigned char)text[i]];
+  return FAMSA_OK;
+}
+
 int famsa_pack_peq(const uint8_t *residues, const int64_t *offsets, int32_t k,
                    int residues_on_device, void *cuda_stream, famsa_family **out) {
   if (!out) return FAMSA_EINVAL;

@@ -511,7 +511,8 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_slink_smem(SmemArgs arg) {
             const int32_t whi = lo <= qb ? (lo << sshift) : e0;
             // binary search inside the window (fewer than 2^sshift positions)
             // through DSMEM: a few dependent loads measured faster than reading
-            // the whole window with independent loads
+            // the whole window, or three quarter points a round trip, with
+            // independent loads (merges are bound by DSMEM traffic)
             int32_t wa = wlo, wb = whi;
             while (wa < wb) {
               const int32_t mid = (wa + wb) >> 1;
