@@ -16,6 +16,7 @@
 #include <atomic>
 #include <chrono>
 #include <mutex>
+#include <numeric>
 #include <vector>
 
 #include "lcs_kernels.cuh"
@@ -124,7 +125,7 @@ struct Batch {
   std::vector<void *> plan_mem;
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> ev;
+  std::vector<cudaEvent_t> ev, ev_stage;
   cudaGraphExec_t exec = nullptr;
   int32_t *d_pi = nullptr, *d_merges = nullptr, *d_sizes = nullptr;
   uint64_t *d_lnum = nullptr, *d_hnum = nullptr;
@@ -141,6 +142,8 @@ static void batch_free_plan(Batch *b) {
   b->exec = nullptr;
   for (auto e : b->ev) cudaEventDestroy(e);
   b->ev.clear();
+  for (auto e : b->ev_stage) cudaEventDestroy(e);
+  b->ev_stage.clear();
   for (auto &e : b->tev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -341,7 +344,10 @@ struct Bucket {
   bool wpp;
   int kw;     // W (thread-per-pair) or NW (warp-per-pair)
   int R = 1;  // rows per tile
-  std::vector<int4> items;
+  // one descriptor per row tile: (first row entry, rows, first column group,
+  // group step); its work items take the column groups gstart + j * gstep
+  std::vector<int4> tiles;
+  std::vector<int32_t> tile_items;
 };
 
 struct BRow {
@@ -358,7 +364,8 @@ struct RowArrays {
 
 static void append_rows(const Batch *b, const std::vector<BRow> &rows, size_t count, bool wpp, int R,
                         const std::vector<int64_t> &h_peq_off, const std::vector<int64_t> &rb_off,
-                        const std::vector<int64_t> &ld, RowArrays &ra, std::vector<int4> &items) {
+                        const std::vector<int64_t> &ld, RowArrays &ra, std::vector<int4> &tiles,
+                        std::vector<int32_t> &tile_items) {
   size_t i = 0;
   while (i < count) {
     const int32_t f = rows[i].f;
@@ -372,15 +379,33 @@ static void append_rows(const Batch *b, const std::vector<BRow> &rows, size_t co
       ra.id.push_back(rid);
       ra.base.push_back(rb_off[f] + (int64_t)(rid - b->S[f] - 1) * ld[f] - b->S[f]);
     }
+    // the tile meets the columns [S[f], rid_last): thread-per-pair items take
+    // 4 column groups (128 columns) each, warp-per-pair items kWppCols columns
     const int32_t rid_last = rows[j - 1].rid;
-    const int32_t g0 = (int32_t)(b->S[f] / kGroup);
-    if (!wpp) {
-      for (int32_t g = g0; g * kGroup < rid_last; g += 4) items.push_back(make_int4(e0, (int)(j - i), g, 0));
-    } else {
-      for (int32_t c = (int32_t)b->S[f]; c < rid_last; c += kWppCols) items.push_back(make_int4(e0, 1, c / kGroup, 0));
-    }
+    const int32_t g0 = (int32_t)(b->S[f] / kGroup);  // S[f] is a multiple of kGroup
+    const int32_t span = rid_last - g0 * kGroup;
+    const int32_t cols = wpp ? kWppCols : 4 * kGroup;
+    tiles.push_back(make_int4(e0, (int)(j - i), g0, cols / kGroup));
+    tile_items.push_back(span > 0 ? (span + cols - 1) / cols : 0);
     i = j;
   }
+}
+
+// Work items from tile descriptors, one warp per tile: item j of tile t is
+// (e0, rows, gstart + j * gstep, 0), written at items[tstart[t] + j].
+__global__ void k_expand_items(const int4 *tiles, const int64_t *tstart, int64_t n_tiles, int4 *items) {
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= n_tiles) return;
+  const int4 d = tiles[t];
+  const int64_t o = tstart[t], n = tstart[t + 1] - o;
+  for (int64_t j = threadIdx.x & 31; j < n; j += 32) items[o + j] = make_int4(d.x, d.y, d.z + (int)j * d.w, 0);
+}
+
+static void expand_on_host(const std::vector<int4> &tiles, const std::vector<int32_t> &tile_items,
+                           std::vector<int4> &items) {
+  for (size_t t = 0; t < tiles.size(); ++t)
+    for (int32_t j = 0; j < tile_items[t]; ++j)
+      items.push_back(make_int4(tiles[t].x, tiles[t].y, tiles[t].z + j * tiles[t].w, 0));
 }
 
 static KParams batch_params(const Batch *b, uint16_t *rowbuf) {
@@ -407,6 +432,13 @@ static KParams batch_params(const Batch *b, uint16_t *rowbuf) {
 // fills the GPU many times over: a sample of a few hundred CTAs favours the
 // smallest R only because it makes more of them.  Another R replaces the
 // default only when it is at least 2% faster.
+// Groups of LCS widths after which row updates may start.  Four groups
+// (updates of the narrow families beside the LCS of the wide buckets) were
+// measured no faster on 512 families: a row-update cluster holds whole SMs
+// while it waits at its barriers, so what it saves at the end it costs the
+// LCS.  One group: every update after the last LCS launch.
+constexpr int kStageGroups = 1;
+
 static std::mutex g_tune_mu;
 static bool g_tuned[kTppMaxW + 1] = {false};
 static std::atomic<int> g_autotune{1};
@@ -418,8 +450,10 @@ static cudaError_t time_rows(const Batch *b, uint16_t *rowbuf, const std::vector
                              const std::vector<int64_t> &rb_off, const std::vector<int64_t> &ld,
                              cudaStream_t st, float *ms) {
   RowArrays ra;
-  std::vector<int4> items;
-  append_rows(b, rows, count, false, R, h_peq_off, rb_off, ld, ra, items);
+  std::vector<int4> tiles, items;
+  std::vector<int32_t> tile_items;
+  append_rows(b, rows, count, false, R, h_peq_off, rb_off, ld, ra, tiles, tile_items);
+  expand_on_host(tiles, tile_items, items);
   int64_t *d_peq = nullptr, *d_base = nullptr;
   int32_t *d_len = nullptr, *d_id = nullptr;
   int4 *d_items = nullptr;
@@ -552,6 +586,47 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       rows_by_bucket[bk].push_back(BRow{rid, f});
     }
   }
+  // buckets in increasing width, and the families in kStageGroups groups by
+  // the last bucket that holds one of their rows: a family's row update can
+  // start as soon as its group's LCS launches are done, beside the LCS of the
+  // wider buckets (groups cut the LCS work into about equal parts)
+  {
+    std::vector<int> order(buckets.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+      return buckets[x].wpp != buckets[y].wpp ? buckets[y].wpp : buckets[x].kw < buckets[y].kw;
+    });
+    std::vector<Bucket> nb;
+    std::vector<std::vector<BRow>> nr;
+    for (int i : order) {
+      nb.push_back(std::move(buckets[i]));
+      nr.push_back(std::move(rows_by_bucket[i]));
+    }
+    buckets.swap(nb);
+    rows_by_bucket.swap(nr);
+  }
+  std::vector<int> bucket_group(buckets.size(), 0), fam_group(F, 0);
+  {
+    std::vector<int64_t> len_pre(b->Kpad + 1, 0);
+    for (int64_t s = 0; s < b->Kpad; ++s) len_pre[s + 1] = len_pre[s] + b->h_slen[s];
+    std::vector<double> work(buckets.size(), 0.0);
+    std::vector<int> fam_last(F, -1);
+    double total = 0.0;
+    for (size_t bk = 0; bk < buckets.size(); ++bk) {
+      for (const BRow &r : rows_by_bucket[bk]) {
+        const int W = (b->h_slen[r.rid] + 63) / 64;
+        work[bk] += (double)W * (double)(len_pre[r.rid] - len_pre[b->S[r.f]]);
+        fam_last[r.f] = std::max(fam_last[r.f], (int)bk);
+      }
+      total += work[bk];
+    }
+    double before = 0.0;
+    for (size_t bk = 0; bk < buckets.size(); ++bk) {
+      bucket_group[bk] = total > 0 ? std::min(kStageGroups - 1, (int)(kStageGroups * before / total)) : 0;
+      before += work[bk];
+    }
+    for (int32_t f = 0; f < F; ++f) fam_group[f] = fam_last[f] < 0 ? 0 : bucket_group[fam_last[f]];
+  }
   // the row blocks (the autotuner's trial launches write into them too)
   cudaError_t pre_err = cudaSuccess;
   uint16_t *rowbuf = A.get<uint16_t>((size_t)rb_off[F]);
@@ -563,28 +638,31 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     Bucket &B = buckets[bk];
     B.R = B.wpp ? 1 : tpp_rows(B.kw);
     append_rows(b, rows_by_bucket[bk], rows_by_bucket[bk].size(), B.wpp, B.R, h_peq_off, rb_off, ld, ra,
-                B.items);
+                B.tiles, B.tile_items);
   }
-  int64_t n_items = 0;
-  for (auto &B : buckets) n_items += (int64_t)B.items.size();
+  // item offsets per bucket and per tile (the items themselves are expanded on the device)
+  std::vector<int64_t> item_off(buckets.size() + 1, 0);
+  std::vector<int4> all_tiles;
+  std::vector<int64_t> tstart(1, 0);
+  for (size_t bk = 0; bk < buckets.size(); ++bk) {
+    const Bucket &B = buckets[bk];
+    all_tiles.insert(all_tiles.end(), B.tiles.begin(), B.tiles.end());
+    for (int32_t c : B.tile_items) tstart.push_back(tstart.back() + c);
+    item_off[bk + 1] = tstart.back();
+  }
+  const int64_t n_items = tstart.back();
   b->stats[0] = cells;
   b->stats[1] = words;
   b->stats[2] = pairs;
   b->stats[3] = n_items;
 
   // device copies of the row arrays and items
-  int64_t *d_rpeq = nullptr, *d_rbase = nullptr;
+  int64_t *d_rpeq = nullptr, *d_rbase = nullptr, *d_tstart = nullptr;
   int32_t *d_rlen = nullptr, *d_rid = nullptr;
-  std::vector<int4> all_items;
-  std::vector<int64_t> item_off(buckets.size() + 1, 0);
-  for (size_t bk = 0; bk < buckets.size(); ++bk) {
-    item_off[bk + 1] = item_off[bk] + (int64_t)buckets[bk].items.size();
-    all_items.insert(all_items.end(), buckets[bk].items.begin(), buckets[bk].items.end());
-  }
-  int4 *d_items = nullptr;
-  std::vector<SmemArgs> smem_args[5];  // cluster sizes 1, 2, 4, 8, 16
+  int4 *d_items = nullptr, *d_tiles = nullptr;
+  std::vector<SmemArgs> smem_args[5][kStageGroups];  // cluster sizes 1, 2, 4, 8, 16 by group
   size_t smem_dyn[5] = {0, 0, 0, 0, 0};
-  struct GlobalFam { SlinkState S; int64_t off, ld; int32_t k; };
+  struct GlobalFam { SlinkState S; int64_t off, ld; int32_t k; int group; };
   std::vector<GlobalFam> global_fams;
   std::vector<BatchInit> inits;
   struct FinJob { int32_t f, k; bool widen; const int32_t *ord; uint64_t *gap, *lam; FinBufs FB; };
@@ -594,7 +672,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   uint64_t *ctl_all = nullptr;
   int64_t n_ctl = 0;
   BatchInit *d_init = nullptr;
-  SmemArgs *d_sargs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  SmemArgs *d_sargs[5][kStageGroups] = {};
   const int max_cl = max_cluster_global();
 
   BCK(pre_err);
@@ -602,7 +680,15 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   BCK(upload_vec(A, ra.base, &d_rbase, st));
   BCK(upload_vec(A, ra.len, &d_rlen, st));
   BCK(upload_vec(A, ra.id, &d_rid, st));
-  BCK(upload_vec(A, all_items, &d_items, st));
+  BCK(upload_vec(A, all_tiles, &d_tiles, st));
+  BCK(upload_vec(A, tstart, &d_tstart, st));
+  d_items = A.get<int4>((size_t)std::max<int64_t>(n_items, 1));
+  if (A.err != cudaSuccess) { err = A.err; goto fail; }
+  if (!all_tiles.empty()) {
+    const int64_t nt = (int64_t)all_tiles.size();
+    k_expand_items<<<(unsigned)((nt + 7) / 8), 256, 0, st>>>(d_tiles, d_tstart, nt, d_items);
+    BCK(cudaGetLastError());
+  }
   // outputs (whole batch)
   b->d_pi = A.get<int32_t>(b->N);
   b->d_lnum = A.get<uint64_t>(b->N);
@@ -668,10 +754,10 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       a.sshift = smem_sample_shift(a.P, a.P * cl);
       a.batch = nullptr;
       a.dyn_bytes = 0;
-      smem_args[ci].push_back(a);
+      smem_args[ci][fam_group[f]].push_back(a);
       smem_dyn[ci] = std::max(smem_dyn[ci], smem_dyn_bytes(a.P, a.P * cl, a.sshift));
     } else {
-      global_fams.push_back(GlobalFam{S, rb_off[f], ld[f], k});
+      global_fams.push_back(GlobalFam{S, rb_off[f], ld[f], k, fam_group[f]});
     }
     const size_t lv = fin_levels(k);
     FinBufs FB = {};
@@ -697,15 +783,24 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   if (A.err != cudaSuccess) { err = A.err; goto fail; }
   BCK(upload_vec(A, inits, &d_init, st));
   for (int ci = 0; ci < 5; ++ci)
-    if (!smem_args[ci].empty()) BCK(upload_vec(A, smem_args[ci], &d_sargs[ci], st));
+    for (int g = 0; g < kStageGroups; ++g)
+      if (!smem_args[ci][g].empty()) BCK(upload_vec(A, smem_args[ci][g], &d_sargs[ci][g], st));
   BCK(cudaStreamSynchronize(st));
 
   // ---- capture the whole pipeline once
   BCK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-  b->side.resize(8);
-  for (auto &s : b->side) BCK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  {
+    // side branches at the highest priority: a row-update cluster takes SMs
+    // as they free up rather than after the whole LCS grid
+    int prio_lo = 0, prio_hi = 0;
+    BCK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    b->side.resize(6 * kStageGroups);
+    for (auto &s : b->side) BCK(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_hi));
+  }
   b->ev.resize(1 + b->side.size());
   for (auto &e : b->ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  b->ev_stage.resize(kStageGroups + 6 * kStageGroups);
+  for (auto &e : b->ev_stage) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (auto &e : b->tev) BCK(cudaEventCreate(&e));
   {
     cudaGraph_t graph = nullptr;
@@ -713,24 +808,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     {
       cudaError_t e = cudaEventRecordWithFlags(b->tev[0], b->cap, cudaEventRecordExternal);
-      // stage I: every family's triangle, one launch per kernel width
-      KParams p = batch_params(b, rowbuf);
-      p.row_peq_off = d_rpeq;
-      p.row_len = d_rlen;
-      p.row_id = d_rid;
-      p.row_base = d_rbase;
-      for (size_t bk = 0; bk < buckets.size() && e == cudaSuccess; ++bk) {
-        const int64_t n = item_off[bk + 1] - item_off[bk];
-        if (n == 0) continue;
-        p.items = d_items + item_off[bk];
-        p.e0 = 0;
-        p.e1 = (int32_t)ra.id.size();
-        e = buckets[bk].wpp ? launch_wpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap)
-                            : launch_tpp(buckets[bk].kw, buckets[bk].R, p, dim3((unsigned)n), b->cap);
-        ++launches;
-      }
-      // stage II: one cluster per family
-      if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[1], b->cap, cudaEventRecordExternal);
+      // the row-update state of every family first (it needs no LCS)
       if (e == cudaSuccess) e = cudaMemsetAsync(ctl_all, 0, sizeof(uint64_t) * n_ctl, b->cap);
       if (e == cudaSuccess && !inits.empty()) {
         k_batch_init<<<nblk((int64_t)inits.size(), T), T, 0, b->cap>>>(
@@ -738,27 +816,55 @@ static int batch_plan(Batch *b, cudaStream_t st) {
         e = cudaGetLastError();
         ++launches;
       }
-      // the launches of each cluster size, and the global-memory families, run
-      // side by side (one branch of the graph each): a launch's tail of large
-      // families no longer holds back the next cluster size
-      if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->cap);
-      for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
-        if (ci < 5 ? smem_args[ci].empty() : global_fams.empty()) continue;
-        cudaStream_t s = b->side[ci];
-        e = cudaStreamWaitEvent(s, b->ev[0], 0);
-        if (e == cudaSuccess && ci < 5) {
-          e = launch_slink_smem_batch(d_sargs[ci], (int32_t)smem_args[ci].size(), 1 << ci, smem_dyn[ci],
-                                      narrow, s);
+      // stage I: every family's triangle, one launch per kernel width in
+      // increasing width; after each group of widths, the row updates of the
+      // families whose rows are all done start on side branches (one per
+      // cluster size, and one for the global-memory families), beside the
+      // LCS of the wider buckets
+      KParams p = batch_params(b, rowbuf);
+      p.row_peq_off = d_rpeq;
+      p.row_len = d_rlen;
+      p.row_id = d_rid;
+      p.row_base = d_rbase;
+      int joins = 0;
+      size_t bk = 0;
+      for (int g = 0; g < kStageGroups && e == cudaSuccess; ++g) {
+        for (; bk < buckets.size() && bucket_group[bk] == g && e == cudaSuccess; ++bk) {
+          const int64_t n = item_off[bk + 1] - item_off[bk];
+          if (n == 0) continue;
+          p.items = d_items + item_off[bk];
+          p.e0 = 0;
+          p.e1 = (int32_t)ra.id.size();
+          e = buckets[bk].wpp ? launch_wpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap)
+                              : launch_tpp(buckets[bk].kw, buckets[bk].R, p, dim3((unsigned)n), b->cap);
           ++launches;
         }
-        for (size_t gi = 0; ci == 5 && gi < global_fams.size() && e == cudaSuccess; ++gi) {
-          const GlobalFam &g = global_fams[gi];
-          e = launch_slink_global(g.S, rowbuf + g.off, g.ld, 1, g.k, max_cl, narrow, s);
-          ++launches;
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_stage[g], b->cap);
+        for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
+          bool any = false;
+          if (ci < 5) any = !smem_args[ci][g].empty();
+          for (size_t gi = 0; ci == 5 && gi < global_fams.size(); ++gi) any = any || global_fams[gi].group == g;
+          if (!any) continue;
+          cudaStream_t s = b->side[6 * g + ci];
+          e = cudaStreamWaitEvent(s, b->ev_stage[g], 0);
+          if (e == cudaSuccess && ci < 5) {
+            e = launch_slink_smem_batch(d_sargs[ci][g], (int32_t)smem_args[ci][g].size(), 1 << ci, smem_dyn[ci],
+                                        narrow, s);
+            ++launches;
+          }
+          for (size_t gi = 0; ci == 5 && gi < global_fams.size() && e == cudaSuccess; ++gi) {
+            const GlobalFam &gf = global_fams[gi];
+            if (gf.group != g) continue;
+            e = launch_slink_global(gf.S, rowbuf + gf.off, gf.ld, 1, gf.k, max_cl, narrow, s);
+            ++launches;
+          }
+          if (e == cudaSuccess) e = cudaEventRecord(b->ev_stage[kStageGroups + joins++], s);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(b->ev[1 + ci], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev[1 + ci], 0);
       }
+      // stage II ends when every branch has joined
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[1], b->cap, cudaEventRecordExternal);
+      for (int j = 0; j < joins && e == cudaSuccess; ++j)
+        e = cudaStreamWaitEvent(b->cap, b->ev_stage[kStageGroups + j], 0);
       // finalisation, spread over side streams
       if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->tev[2], b->cap, cudaEventRecordExternal);
       if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->cap);
@@ -788,7 +894,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
         goto fail;
       }
     }
-    err = cudaGraphInstantiate(&b->exec, graph, 0);
+    err = cudaGraphInstantiateWithFlags(&b->exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) goto fail;
     b->stats[4] = launches;

@@ -505,13 +505,17 @@ static cudaError_t launch_global_t(const GlobalArgs &args, int cl, cudaStream_t 
   cfg.blockDim = dim3(T, 1, 1);
   cfg.dynamicSmemBytes = global_smem_bytes<T, E>();
   cfg.stream = st;
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = cl;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
+  int prio = 0;  // kept by a captured graph node (see launch_smem_t)
+  cudaStreamGetPriority(st, &prio);
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_slink_global<K, T, E>, args);
 }
 

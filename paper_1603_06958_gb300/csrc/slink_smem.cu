@@ -768,13 +768,19 @@ static cudaError_t launch_smem_t(const SmemArgs &args, int cl, cudaStream_t st, 
   cfg.blockDim = dim3(g_smem_threads, 1, 1);
   cfg.dynamicSmemBytes = dyn;
   cfg.stream = st;
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = cl;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
+  // the stream's priority travels with the launch, so that a captured graph
+  // node keeps it (graphs instantiated with node priorities)
+  int prio = 0;
+  cudaStreamGetPriority(st, &prio);
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_slink_smem<K>, args);
 }
 
