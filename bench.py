@@ -390,7 +390,11 @@ def run_batch(args, rank, world, local_rank):
                                     "finalise": float(np.mean([s["finalize_ns"] for s in stats])) / 1e6,
                                     "graph_only": float(np.mean(graph_ms)),
                                     "pack": float(np.mean(pack_ms)),
-                                    "plan_and_capture": ms_step - float(np.mean(pack_ms)) - float(np.mean(graph_ms))},
+                                    "plan_and_capture": ms_step - float(np.mean(pack_ms)) - float(np.mean(graph_ms)),
+                                    "plan_host": float(np.mean([s["plan_host_ns"] for s in stats])) / 1e6,
+                                    "capture": float(np.mean([s["capture_ns"] for s in stats])) / 1e6,
+                                    "instantiate": float(np.mean([s["instantiate_ns"] for s in stats])) / 1e6},
+                   "graph_nodes": int(stats[-1]["graph_nodes"]),
                    "graph_only_gcups": cells / (float(np.mean(graph_ms)) * 1e-3) / 1e9,
                    "plain_ms": plain_ms,
                    "plain_gcups": (cells / (plain_ms * 1e-3) / 1e9) if plain_ms else None,

@@ -248,17 +248,20 @@ int famsa_batch_tree(famsa_batch *b, int32_t *pi, uint64_t *lambda_num, uint32_t
                      int32_t *merges, uint64_t *h_num, uint32_t *h_den, int32_t *sizes,
                      int out_on_device, void *cuda_stream);
 
-/* Counters of the batch plan, stats[12] int64: 0 LCS cells (sum of |A||B|
+/* Counters of the batch plan, stats[16] int64: 0 LCS cells (sum of |A||B|
  * over every family's pairs), 1 LCS word steps, 2 pairs, 3 LCS work items,
  * 4 kernel launches captured in the graph, 5 LCS kernel widths, 6 families
  * on the global-memory row update, 7..9 device time in ns of the LCS, the
  * row update and the finalisation in the last graph launch (this call waits
  * for that launch), 10 kernel widths the autotuner timed for this plan, 11
- * ns the autotuner took.  Zero before the first tree.
+ * ns the autotuner took, 12 ns of host planning before the graph capture
+ * (autotuner included), 13 ns of the capture, 14 ns of the graph
+ * instantiation, 15 graph nodes.  Zero before the first tree.
  *
  * The autotuner: the first plan with at least 64 rows of a thread-per-pair
  * width times each allowed rows-per-tile choice (1, 2 or 4 rows, with rows
- * x words <= 32) on the same 1,024-row sample and keeps the fastest for the
+ * x words <= 32) on the same sample of its rows (about 4e9 word steps) and
+ * keeps the default unless another choice is at least 2 % faster, for the
  * process, for batches and single families alike; results do not depend on
  * the choice. */
 int famsa_batch_stats(const famsa_batch *b, int64_t *stats);

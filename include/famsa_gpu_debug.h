@@ -80,6 +80,11 @@ int famsa_debug_set_global_variant(int v);
  * and FMA pipes for the LCS roofline.  Allocates a small output buffer. */
 int famsa_debug_int_pipe_rate(int kind, double *inst_per_s);
 
+/* on != 0 (default): families of up to 4,096 points are finalised by one
+ * CTA in one launch; 0: every family takes the multi-kernel finalisation.
+ * Both give the same outputs.  Returns FAMSA_OK. */
+int famsa_debug_set_fin_small(int on);
+
 /* The row update's exact order code of the distance num / den (den in
  * 1..32767, num < 2^32): floor(num * 2^30 / den), and back from a code to the
  * distance as a reduced fraction.  Host-only arithmetic, no GPU needed;

@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
             "famsa_debug_int_pipe_rate": ([ctypes.c_int, _P], ctypes.c_int),
             "famsa_debug_set_global_variant": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_fin_small": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_order_code": ([ctypes.c_uint32, ctypes.c_uint32, _P], ctypes.c_int),
             "famsa_debug_code_fraction": ([ctypes.c_uint64, _P, _P], ctypes.c_int),
             "famsa_debug_set_tpp_rows": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -314,11 +315,11 @@ class Batch:
             pass
 
     def stats(self) -> dict:
-        s = np.zeros(12, dtype=np.int64)
+        s = np.zeros(16, dtype=np.int64)
         _check(load().famsa_batch_stats(self.handle, s.ctypes.data), "famsa_batch_stats")
         keys = ["cells", "word_steps", "pairs", "lcs_items", "graph_launches", "lcs_widths",
                 "global_update_families", "lcs_ns", "update_ns", "finalize_ns", "tuned_widths",
-                "tune_ns"]
+                "tune_ns", "plan_host_ns", "capture_ns", "instantiate_ns", "graph_nodes"]
         return {k: int(v) for k, v in zip(keys, s)}
 
 
@@ -580,6 +581,11 @@ def debug_code_fraction(code: int) -> tuple:
     _check(load().famsa_debug_code_fraction(int(code), ctypes.byref(num), ctypes.byref(den)),
            "famsa_debug_code_fraction")
     return int(num.value), int(den.value)
+
+
+def debug_set_fin_small(on: bool):
+    """True (default): one-launch finalisation up to 4,096 points; False: multi-kernel always."""
+    _check(load().famsa_debug_set_fin_small(int(on)), "famsa_debug_set_fin_small")
 
 
 def debug_set_cluster(ctas: int):

@@ -133,7 +133,7 @@ struct Batch {
   // graph start, LCS, update, end: recorded by event-record nodes of the graph
   cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool launched = false;
-  int64_t stats[12] = {0};
+  int64_t stats[16] = {0};
   std::mutex mu;
 };
 
@@ -538,6 +538,10 @@ static cudaError_t autotune_rows(Batch *b, uint16_t *rowbuf, const std::vector<B
 
 static int batch_plan(Batch *b, cudaStream_t st) {
   AllocStream alloc_on(st);
+  const auto t_plan0 = std::chrono::steady_clock::now();
+  auto ns_since = [](std::chrono::steady_clock::time_point t) {
+    return (int64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t).count();
+  };
   const int32_t F = b->F;
   RowArrays ra;  // row entries of every bucket, concatenated
   Arena A{&b->plan_mem};
@@ -665,7 +669,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   struct GlobalFam { SlinkState S; int64_t off, ld; int32_t k; int group; };
   std::vector<GlobalFam> global_fams;
   std::vector<BatchInit> inits;
-  struct FinJob { int32_t f, k; bool widen; const int32_t *ord; uint64_t *gap, *lam; FinBufs FB; };
+  struct FinJob { int32_t f, k; bool widen; const int32_t *ord; uint64_t *gap; FinBufs FB; };
   std::vector<FinJob> fins;
   const bool narrow = b->max_len <= 32767;
   const uint64_t inf_narrow = KeysNarrow::kInf, inf_wide = KeysWide::kInf;
@@ -778,7 +782,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     FB.hden = b->d_hden + om;
     FB.sizes = b->d_sizes + om;
     const int bk = k & 1;
-    fins.push_back(FinJob{f, k, narrow, S.ord[bk], S.gap[bk], S.lam[bk], FB});
+    fins.push_back(FinJob{f, k, narrow, S.ord[bk], S.gap[bk], FB});
   }
   if (A.err != cudaSuccess) { err = A.err; goto fail; }
   BCK(upload_vec(A, inits, &d_init, st));
@@ -805,6 +809,8 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   {
     cudaGraph_t graph = nullptr;
     int64_t launches = 0;
+    b->stats[12] = ns_since(t_plan0);
+    const auto t_cap0 = std::chrono::steady_clock::now();
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     {
       cudaError_t e = cudaEventRecordWithFlags(b->tev[0], b->cap, cudaEventRecordExternal);
@@ -873,13 +879,7 @@ static int batch_plan(Batch *b, cudaStream_t st) {
       for (size_t j = 0; j < fins.size() && e == cudaSuccess; ++j) {
         FinJob &J = fins[j];
         cudaStream_t s = b->side[j % b->side.size()];
-        if (J.widen) {
-          e = widen_keys(J.gap, J.k - 1, s);
-          if (e == cudaSuccess) e = widen_keys(J.lam, J.k, s);
-          launches += 2;
-        }
-        if (e == cudaSuccess)
-          e = launch_finalize(J.ord, J.gap, b->d_perm_local + b->S[J.f], J.k, J.FB, s, &launches);
+        e = launch_finalize(J.ord, J.gap, b->d_perm_local + b->S[J.f], J.k, J.FB, s, &launches, J.widen);
       }
       for (size_t i = 0; i < b->side.size() && e == cudaSuccess; ++i) {
         e = cudaEventRecord(b->ev[1 + i], b->side[i]);
@@ -894,7 +894,14 @@ static int batch_plan(Batch *b, cudaStream_t st) {
         goto fail;
       }
     }
+    b->stats[13] = ns_since(t_cap0);
+    {
+      size_t nodes = 0;
+      if (cudaGraphGetNodes(graph, nullptr, &nodes) == cudaSuccess) b->stats[15] = (int64_t)nodes;
+    }
+    const auto t_inst0 = std::chrono::steady_clock::now();
     err = cudaGraphInstantiateWithFlags(&b->exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    b->stats[14] = ns_since(t_inst0);
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) goto fail;
     b->stats[4] = launches;
@@ -973,7 +980,7 @@ int famsa_batch_stats(const famsa_batch *bh, int64_t *stats) {
     if (err != cudaSuccess) return status_from_cuda(err);
     for (int i = 0; i < 3; ++i) b->stats[7 + i] = (int64_t)(ms[i] * 1e6);
   }
-  for (int i = 0; i < 12; ++i) stats[i] = b->stats[i];
+  for (int i = 0; i < 16; ++i) stats[i] = b->stats[i];
   return FAMSA_OK;
 }
 

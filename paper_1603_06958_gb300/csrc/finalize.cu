@@ -24,22 +24,22 @@ namespace famsa {
 
 __global__ void k_scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t *total);
 
-__global__ void k_fin_idx(const int32_t *ord, const int32_t *perm, int32_t k, int32_t *idx) {
-  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < k) idx[p] = perm[ord[p]];
+// ---- per-element steps, shared by the multi-kernel path (one launch per
+// step) and the single-CTA path (every step in one launch)
+
+__device__ __forceinline__ void fin_idx_at(int32_t p, const int32_t *ord, const int32_t *perm, int32_t *idx) {
+  idx[p] = perm[ord[p]];
 }
 
 // level j of the range-max tables: T[j][p] = max over [p, p + 2^j)
-__global__ void k_fin_level(uint64_t *gt, int32_t *it, int32_t k, int32_t j) {
-  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fin_level_at(int32_t p, uint64_t *gt, int32_t *it, int32_t k, int32_t j) {
   const int32_t h = 1 << (j - 1);
   const int64_t K = k;
   if (p + 2 * h <= k - 1) gt[j * K + p] = kmax(gt[(j - 1) * K + p], gt[(j - 1) * K + p + h]);
   if (p + 2 * h <= k) it[j * K + p] = max(it[(j - 1) * K + p], it[(j - 1) * K + p + h]);
 }
 
-__global__ void k_fin_level_int(int32_t *rt, int32_t k, int32_t j) {
-  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fin_level_int_at(int32_t p, int32_t *rt, int32_t k, int32_t j) {
   const int32_t h = 1 << (j - 1);
   const int64_t K = k;
   if (p + 2 * h <= k) rt[j * K + p] = max(rt[(j - 1) * K + p], rt[(j - 1) * K + p + h]);
@@ -57,12 +57,10 @@ __device__ __forceinline__ int32_t int_max(const int32_t *t, int64_t K, int32_t 
   return max(t[j * K + a], t[j * K + b - (1 << j) + 1]);
 }
 
-// lambda, pi and the pointer-subtree interval of each point
-__global__ void k_fin_lambda(const uint64_t *gt, const int32_t *it, const int32_t *idx, int32_t k,
-                             int levels, uint64_t *lam, int32_t *pi, int32_t *sub_lo,
-                             int32_t *sub_hi) {
-  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= k) return;
+// lambda, pi and the pointer-subtree interval of the point at position p
+__device__ __forceinline__ void fin_lambda_at(int32_t p, const uint64_t *gt, const int32_t *it,
+                                              const int32_t *idx, int32_t k, int levels, uint64_t *lam,
+                                              int32_t *pi, int32_t *sub_lo, int32_t *sub_hi) {
   const int64_t K = k;
   const int32_t j = idx[p];
   uint64_t L = kKeyInf;
@@ -121,11 +119,10 @@ struct ByParent {
   }
 };
 
-// bottom-up merge pass on an index array under a strict total order
+// one element of a bottom-up merge pass on an index array under a strict total order
 template <class Cmp>
-__global__ void k_msort(const int32_t *in, int32_t *out, int32_t n, int32_t width, Cmp cmp) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void msort_at(int32_t i, const int32_t *in, int32_t *out, int32_t n, int32_t width,
+                                         Cmp cmp) {
   int64_t run = i / width;
   int64_t start = run * width;
   int64_t pair_start = (run & ~1LL) * width;
@@ -141,37 +138,11 @@ __global__ void k_msort(const int32_t *in, int32_t *out, int32_t n, int32_t widt
   out[pair_start + (i - start) + (lo - pstart)] = x;
 }
 
-__global__ void k_fin_iota(int32_t *a, int32_t n) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] = i;
-}
-
-__global__ void k_fin_rank(const int32_t *order, int32_t n, int32_t *rank) {
-  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) rank[order[t]] = t;
-}
-
-__global__ void k_fin_rankpos(const int32_t *idx, const int32_t *rank, int32_t k, int32_t *rt0) {
-  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < k) rt0[p] = idx[p] == k - 1 ? -1 : rank[idx[p]];
-}
-
-__global__ void k_fin_sizes(const int32_t *sorder, const int32_t *sub_lo, const int32_t *sub_hi,
-                            int32_t n, int64_t *sz) {
-  int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) {
-    int32_t j = sorder[s];
-    sz[s] = sub_hi[j] - sub_lo[j] + 1;
-  }
-}
-
-__global__ void k_fin_merges(const int32_t *sorder, const int32_t *pi, const uint64_t *lam,
-                             const int32_t *rank, const int32_t *sub_lo, const int32_t *sub_hi,
-                             const int32_t *posof, const int32_t *rt, const int64_t *szpre,
-                             int32_t n, int32_t k, int32_t *merges, uint64_t *hkey,
-                             int32_t *sizes) {
-  int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+__device__ __forceinline__ void fin_merges_at(int32_t s, const int32_t *sorder, const int32_t *pi,
+                                              const uint64_t *lam, const int32_t *rank,
+                                              const int32_t *sub_lo, const int32_t *sub_hi,
+                                              const int32_t *posof, const int32_t *rt, const int64_t *szpre,
+                                              int32_t k, int32_t *merges, uint64_t *hkey, int32_t *sizes) {
   const int64_t K = k;
   const int32_t j = sorder[s];
   const int32_t par = pi[j];
@@ -208,20 +179,13 @@ __global__ void k_fin_merges(const int32_t *sorder, const int32_t *pi, const uin
   sizes[t] = (int32_t)(sz_j + 1 + before);
 }
 
-__global__ void k_fin_posof(const int32_t *idx, int32_t k, int32_t *posof) {
-  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < k) posof[idx[p]] = p;
-}
-
 __device__ uint64_t gcd_u64(uint64_t a, uint64_t b) {
   while (b) { uint64_t t = a % b; a = b; b = t; }
   return a;
 }
 
 // packed key -> reduced (num, den)
-__global__ void k_fin_reduce(const uint64_t *key, int32_t n, uint64_t *num, uint32_t *den) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void fin_reduce_at(int32_t i, const uint64_t *key, uint64_t *num, uint32_t *den) {
   uint64_t kk = key[i];
   uint64_t nu = kk >> 16;
   uint32_t de = (uint32_t)(kk & 0xffffu);
@@ -236,20 +200,208 @@ __global__ void k_fin_reduce(const uint64_t *key, int32_t n, uint64_t *num, uint
   den[i] = de;
 }
 
+// ---- the multi-kernel path: one launch per step
+#define FIN_ELEMENTWISE(name, n_expr)                         \
+  const int32_t name = blockIdx.x * blockDim.x + threadIdx.x; \
+  if (name >= (n_expr)) return;
+
+__global__ void k_fin_widen(uint64_t *key, int32_t n) {
+  FIN_ELEMENTWISE(i, n)
+  key[i] = KeysNarrow::wide(key[i]);
+}
+__global__ void k_fin_idx(const int32_t *ord, const int32_t *perm, int32_t k, int32_t *idx) {
+  FIN_ELEMENTWISE(p, k)
+  fin_idx_at(p, ord, perm, idx);
+}
+__global__ void k_fin_level(uint64_t *gt, int32_t *it, int32_t k, int32_t j) {
+  FIN_ELEMENTWISE(p, k)
+  fin_level_at(p, gt, it, k, j);
+}
+__global__ void k_fin_level_int(int32_t *rt, int32_t k, int32_t j) {
+  FIN_ELEMENTWISE(p, k)
+  fin_level_int_at(p, rt, k, j);
+}
+__global__ void k_fin_lambda(const uint64_t *gt, const int32_t *it, const int32_t *idx, int32_t k,
+                             int levels, uint64_t *lam, int32_t *pi, int32_t *sub_lo,
+                             int32_t *sub_hi) {
+  FIN_ELEMENTWISE(p, k)
+  fin_lambda_at(p, gt, it, idx, k, levels, lam, pi, sub_lo, sub_hi);
+}
+template <class Cmp>
+__global__ void k_msort(const int32_t *in, int32_t *out, int32_t n, int32_t width, Cmp cmp) {
+  FIN_ELEMENTWISE(i, n)
+  msort_at(i, in, out, n, width, cmp);
+}
+__global__ void k_fin_iota(int32_t *a, int32_t n) {
+  FIN_ELEMENTWISE(i, n)
+  a[i] = i;
+}
+__global__ void k_fin_rank(const int32_t *order, int32_t n, int32_t *rank) {
+  FIN_ELEMENTWISE(t, n)
+  rank[order[t]] = t;
+}
+__global__ void k_fin_rankpos(const int32_t *idx, const int32_t *rank, int32_t k, int32_t *rt0) {
+  FIN_ELEMENTWISE(p, k)
+  rt0[p] = idx[p] == k - 1 ? -1 : rank[idx[p]];
+}
+__global__ void k_fin_sizes(const int32_t *sorder, const int32_t *sub_lo, const int32_t *sub_hi,
+                            int32_t n, int64_t *sz) {
+  FIN_ELEMENTWISE(s, n)
+  const int32_t j = sorder[s];
+  sz[s] = sub_hi[j] - sub_lo[j] + 1;
+}
+__global__ void k_fin_merges(const int32_t *sorder, const int32_t *pi, const uint64_t *lam,
+                             const int32_t *rank, const int32_t *sub_lo, const int32_t *sub_hi,
+                             const int32_t *posof, const int32_t *rt, const int64_t *szpre,
+                             int32_t n, int32_t k, int32_t *merges, uint64_t *hkey,
+                             int32_t *sizes) {
+  FIN_ELEMENTWISE(s, n)
+  fin_merges_at(s, sorder, pi, lam, rank, sub_lo, sub_hi, posof, rt, szpre, k, merges, hkey, sizes);
+}
+__global__ void k_fin_posof(const int32_t *idx, int32_t k, int32_t *posof) {
+  FIN_ELEMENTWISE(p, k)
+  posof[idx[p]] = p;
+}
+__global__ void k_fin_reduce(const uint64_t *key, int32_t n, uint64_t *num, uint32_t *den) {
+  FIN_ELEMENTWISE(i, n)
+  fin_reduce_at(i, key, num, den);
+}
+#undef FIN_ELEMENTWISE
+
+// ---- the single-CTA path: every step of one family in one launch, the
+// steps separated by block barriers (families up to kFinSmall points)
+constexpr int kFinSmall = 4096;
+constexpr int kFinThreads = 1024;
+static int g_fin_small = kFinSmall;  // test hook: 0 sends every family to the multi-kernel path
+
+#define FIN_FOR(v, n) for (int32_t v = (int32_t)threadIdx.x; v < (n); v += kFinThreads)
+
+// exclusive prefix sums of in[0, n) into out, total into *total (one block)
+__device__ void fin_block_scan(const int64_t *in, int64_t *out, int32_t n, int64_t *total, int64_t *warp_sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // each thread takes a contiguous chunk, then the chunk sums are scanned
+  const int32_t chunk = (n + kFinThreads - 1) / kFinThreads;
+  const int32_t b = min(n, (int32_t)threadIdx.x * chunk), e = min(n, b + chunk);
+  int64_t sum = 0;
+  for (int32_t i = b; i < e; ++i) sum += in[i];
+  int64_t x = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = warp_sums[lane];  // kFinThreads / 32 == 32 warps
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    warp_sums[lane] = w;
+  }
+  __syncthreads();
+  int64_t run = x - sum + (warp > 0 ? warp_sums[warp - 1] : 0);
+  for (int32_t i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (threadIdx.x == kFinThreads - 1) *total = run;
+}
+
+__global__ void __launch_bounds__(kFinThreads, 1) k_fin_small(const int32_t *ord, uint64_t *gap, const int32_t *perm,
+                                                           int32_t k, int widen, FinBufs B) {
+  __shared__ int64_t warp_sums[32];
+  const int levels = ilog2(k) + 1;  // the number of levels fin_levels gives
+  const int64_t K = k;
+  const int32_t n = k - 1;
+  if (widen) {
+    FIN_FOR(i, n) gap[i] = KeysNarrow::wide(gap[i]);
+    __syncthreads();
+  }
+  FIN_FOR(p, k) fin_idx_at(p, ord, perm, B.idx);
+  __syncthreads();
+  FIN_FOR(p, k) {
+    B.posof[B.idx[p]] = p;
+    B.it[p] = B.idx[p];
+    if (p < n) B.gt[p] = gap[p];
+  }
+  __syncthreads();
+  for (int j = 1; j < levels; ++j) {
+    FIN_FOR(p, k) fin_level_at(p, B.gt, B.it, k, j);
+    __syncthreads();
+  }
+  FIN_FOR(p, k) fin_lambda_at(p, B.gt, B.it, B.idx, k, levels, B.lam, B.pi, B.sub_lo, B.sub_hi);
+  FIN_FOR(i, n) {
+    B.ordA[i] = i;
+    B.sorder[i] = i;
+  }
+  __syncthreads();
+  // merge order (lambda, j), then sibling order (pi, lambda, j)
+  int32_t *a = B.ordA, *b = B.ordB;
+  for (int32_t w = 1; w < n; w *= 2) {
+    FIN_FOR(i, n) msort_at(i, a, b, n, w, ByLambda{B.lam});
+    __syncthreads();
+    int32_t *t = a; a = b; b = t;
+  }
+  FIN_FOR(t, n) B.rank[a[t]] = t;
+  __syncthreads();
+  FIN_FOR(p, k) B.rt[p] = B.idx[p] == k - 1 ? -1 : B.rank[B.idx[p]];
+  __syncthreads();
+  for (int j = 1; j < levels; ++j) {
+    FIN_FOR(p, k) fin_level_int_at(p, B.rt, k, j);
+    __syncthreads();
+  }
+  int32_t *c = B.sorder, *d = b;  // b: the free one of ordA / ordB
+  for (int32_t w = 1; w < n; w *= 2) {
+    FIN_FOR(i, n) msort_at(i, c, d, n, w, ByParent{B.pi, B.lam});
+    __syncthreads();
+    int32_t *t = c; c = d; d = t;
+  }
+  FIN_FOR(s, n) {
+    const int32_t j = c[s];
+    B.sz[s] = B.sub_hi[j] - B.sub_lo[j] + 1;
+  }
+  __syncthreads();
+  fin_block_scan(B.sz, B.szpre, n, B.tot, warp_sums);
+  __syncthreads();
+  FIN_FOR(s, n)
+    fin_merges_at(s, c, B.pi, B.lam, B.rank, B.sub_lo, B.sub_hi, B.posof, B.rt, B.szpre, k, B.merges, B.hkey,
+                  B.sizes);
+  FIN_FOR(i, k) fin_reduce_at(i, B.lam, B.lnum, B.lden);
+  __syncthreads();
+  FIN_FOR(i, n) fin_reduce_at(i, B.hkey, B.hnum, B.hden);
+  (void)K;
+}
+#undef FIN_FOR
+
 size_t fin_levels(int32_t k) {
   int l = 1;
   while ((1 << l) <= k) ++l;
   return (size_t)l;
 }
 
-// Enqueue the finalisation for a layout of k >= 2 points; returns launches via *launches.
-cudaError_t launch_finalize(const int32_t *ord, const uint64_t *gap, const int32_t *perm, int32_t k,
-                            FinBufs &B, cudaStream_t st, int64_t *launches) {
+// Enqueue the finalisation for a layout of k >= 2 points; returns launches via
+// *launches.  With widen, the gaps are order codes and are first turned into
+// wide keys in place.  Up to kFinSmall points one CTA runs every step in one
+// launch (the same per-element steps, separated by block barriers).
+cudaError_t launch_finalize(const int32_t *ord, uint64_t *gap, const int32_t *perm, int32_t k,
+                            FinBufs &B, cudaStream_t st, int64_t *launches, bool widen) {
+  if (k <= g_fin_small) {
+    k_fin_small<<<1, kFinThreads, 0, st>>>(ord, gap, perm, k, widen ? 1 : 0, B);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+  }
   const int T = 256;
   const unsigned nb = (unsigned)((k + T - 1) / T);
   const int levels = (int)fin_levels(k);
   const int64_t K = k;
   int64_t L = 0;
+  if (widen) {
+    k_fin_widen<<<(unsigned)((k - 1 + T - 1) / T), T, 0, st>>>(gap, k - 1);
+    ++L;
+  }
   k_fin_idx<<<nb, T, 0, st>>>(ord, perm, k, B.idx);
   k_fin_posof<<<nb, T, 0, st>>>(B.idx, k, B.posof);
   cudaMemcpyAsync(B.gt, gap, sizeof(uint64_t) * (k - 1), cudaMemcpyDeviceToDevice, st);
@@ -301,3 +453,8 @@ cudaError_t launch_finalize(const int32_t *ord, const uint64_t *gap, const int32
 }
 
 }  // namespace famsa
+
+extern "C" int famsa_debug_set_fin_small(int on) {
+  famsa::g_fin_small = on ? famsa::kFinSmall : 0;
+  return FAMSA_OK;
+}

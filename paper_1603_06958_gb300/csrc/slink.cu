@@ -206,12 +206,11 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     }
     // finalisation from the layout of k points (buffer k & 1), keys in the wide packing
     CKE(timing_event(sB));
-    if (narrow) {
-      CKE(widen_keys(S.gap[k & 1], k - 1, sB));
-      CKE(widen_keys(S.lam[k & 1], k, sB));
-    }
+    // (the streamed lambda is widened for the debug export; the finalisation
+    // widens the gaps itself)
+    if (narrow) CKE(widen_keys(S.lam[k & 1], k, sB));
     if (k >= 2) {
-      CKE(launch_finalize(S.ord[k & 1], S.gap[k & 1], f->d_perm, k, FB, sB, &launches));
+      CKE(launch_finalize(S.ord[k & 1], S.gap[k & 1], f->d_perm, k, FB, sB, &launches, narrow));
     } else {
       std::vector<int32_t> z = {0};
       std::vector<uint64_t> one = {1};

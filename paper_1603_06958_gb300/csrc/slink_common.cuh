@@ -321,8 +321,8 @@ struct FinBufs {
 };
 
 size_t fin_levels(int32_t k);
-cudaError_t launch_finalize(const int32_t *ord, const uint64_t *gap, const int32_t *perm, int32_t k,
-                            FinBufs &B, cudaStream_t st, int64_t *launches);
+cudaError_t launch_finalize(const int32_t *ord, uint64_t *gap, const int32_t *perm, int32_t k,
+                            FinBufs &B, cudaStream_t st, int64_t *launches, bool widen);
 cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,
                                 int32_t r1, int cl, bool narrow, cudaStream_t st);
 int max_cluster_global();

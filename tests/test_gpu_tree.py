@@ -29,6 +29,7 @@ def fg():
     m.debug_set_cluster(0)
     m.debug_set_update_path(0)
     m.debug_set_update_threads(0)
+    m.debug_set_fin_small(True)
 
 
 def oracle_tree(res, off):
@@ -74,6 +75,26 @@ def test_tree_matches_oracle(fg, case):
     res, off = synth.family(case.pop("k"), case.pop("seed"), **case)
     got, _ = run_tree(fg, res, off)
     assert_same_tree(got, oracle_tree(res, off))
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[5]],
+                         ids=lambda c: "k%d_s%d" % (c["k"], c["seed"]))
+def test_one_launch_and_multi_kernel_finalisation_agree(fg, case):
+    # families of up to 4,096 points are finalised by one CTA in one launch;
+    # the multi-kernel path must give the same tree on the same families
+    # (tie-heavy ones included), and both the oracle's
+    case = dict(case)
+    res, off = synth.family(case.pop("k"), case.pop("seed"), **case)
+    want = oracle_tree(res, off)
+    one, st1 = run_tree(fg, res, off)
+    fg.debug_set_fin_small(False)
+    try:
+        multi, st2 = run_tree(fg, res, off)
+    finally:
+        fg.debug_set_fin_small(True)
+    assert_same_tree(one, want)
+    assert_same_tree(multi, want)
+    assert st1["launches"] < st2["launches"]
 
 
 def test_degenerate_families(fg):
