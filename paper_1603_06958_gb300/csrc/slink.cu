@@ -1,11 +1,11 @@
 // famsa_slink_tree host driver: LCS row blocks on one stream, the SLINK row
-// update on a second (higher-priority) stream, double-buffered row storage so
-// the LCS of block b+1 overlaps the row update of block b, then the parallel
-// finalisation.
+// update on a second (higher-priority) stream, kRowBuffers row blocks in
+// flight so the LCS of the next blocks overlaps the row update of block b,
+// then the parallel finalisation.
 //
 // FAMSA Methods, "Determination of the guide tree": stages I and II run
 // together -- each similarity row feeds the single-linkage update as soon as
-// it exists, so the k x k matrix is never stored (O(k) tree state plus two
+// it exists, so the k x k matrix is never stored (O(k) tree state plus a few
 // row blocks).
 //
 // Points are inserted in the family's length-sorted order (the order the LCS
