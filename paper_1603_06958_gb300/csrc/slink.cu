@@ -166,8 +166,11 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       }
     }
     int32_t blk = 0;
-    for (int32_t r0 = 1; r0 < k; r0 += B, ++blk) {
-      const int32_t r1 = std::min(r0 + B, k);
+    // the first block is an eighth of the others: the row update can start
+    // once its few, short rows are done
+    const int32_t B0 = std::min(B, std::max(B / 8, 64));  // the buffers hold B rows
+    for (int32_t r0 = 1, r1 = 0; r0 < k; r0 = r1, ++blk) {
+      r1 = std::min(r0 + (blk == 0 ? B0 : B), k);
       const int buf = blk % kRowBuffers;
       if (blk >= kRowBuffers) CKE(cudaStreamWaitEvent(sA, upd_done[buf], 0));
       if (g_serial && blk >= 1) CKE(cudaStreamWaitEvent(sA, upd_done[(blk - 1) % kRowBuffers], 0));
