@@ -126,3 +126,35 @@ def test_batch_argument_errors(fg):
     bad[3] = 25
     with pytest.raises(fg.FamsaError):
         fg.batch_pack(bad, o, np.array([0, 5, 10]))       # residue code out of range
+
+
+def test_batch512_full_size_sampled(fg):
+    # the 512-family batch the bench times, through the same graph: the
+    # families the oracle finishes quickly (all pairs up to 3e9 cells) equal
+    # its trees exactly, a spread of others equal the single-family call, and
+    # every family satisfies the tree invariants
+    import torch
+    fams = synth.batch512(1)
+    res, off, fo = concat(fams)
+    b = fg.batch_pack(torch.from_numpy(res).cuda(), torch.from_numpy(off).cuda(), fo)
+    out = fg.batch_tree(b)
+    cells = []
+    for r, o in fams:
+        lens = np.diff(o).astype(np.float64)
+        cells.append((lens.sum() ** 2 - (lens ** 2).sum()) / 2)
+    cheap = [f for f in np.argsort(cells) if cells[f] <= 3e9][:12]
+    assert len(cheap) >= 8
+    for f in cheap:
+        r, o = fams[f]
+        assert_same(fg.batch_family_tree(out, b, int(f)), oracle.tree(r, o), ("oracle", int(f)))
+    for f in (3, 97, 200, 311, 448, 511):
+        r, o = fams[f]
+        assert_same(fg.batch_family_tree(out, b, f), alone(fg, r, o), ("alone", f))
+    for f in range(len(fams)):
+        t = fg.batch_family_tree(out, b, f)
+        k = len(fams[f][1]) - 1
+        pi = np.asarray(t["pi"], dtype=np.int64)
+        assert (pi[:-1] > np.arange(k - 1)).all() and pi[-1] == k - 1, f
+        sizes = np.asarray(t["sizes"], dtype=np.int64)
+        assert k == 1 or sizes[-1] == k, f
+    b.free()
