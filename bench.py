@@ -696,6 +696,23 @@ def run_int_peaks():
     return 0
 
 
+def run_cluster_probe():
+    """SM clocks of the row update's building blocks on 1- and 16-CTA clusters."""
+    import paper_1603_06958_gb300 as fg
+    fg.load()
+    names = ["block_scan_order_codes", "block_scan_cross_multiplied", "cluster_barrier",
+             "push_to_every_cta_and_barrier", "dependent_local_smem_load", "dependent_dsmem_load"]
+    out = {}
+    for cl in (1, 16):
+        row = {}
+        for kind, name in enumerate(names):
+            fg.debug_cluster_probe(kind, cl)  # warm-up
+            row[name] = float(np.median([fg.debug_cluster_probe(kind, cl) for _ in range(5)]))
+        out["cluster_%d" % cl] = row
+    print(json.dumps({"unit": "SM clocks per repetition", "threads_per_cta": 512, **out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,6 +733,8 @@ def main():
                     help="global-memory row update: -1 by size (default), 0 = 1,024 threads a CTA, 1 = 512")
     ap.add_argument("--no-plain", action="store_true",
                     help="batch512: skip timing the one-family-at-a-time comparator")
+    ap.add_argument("--cluster-probe", action="store_true",
+                    help="time the row update's building blocks (scans, barriers, DSMEM) and exit")
     ap.add_argument("--int-peaks", action="store_true",
                     help="measure the integer pipe widths used by the roofline, then exit")
     args = ap.parse_args()
@@ -726,6 +745,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.int_peaks:
         return run_int_peaks()
+    if args.cluster_probe:
+        return run_cluster_probe()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:

@@ -80,6 +80,15 @@ int famsa_debug_set_global_variant(int v);
  * and FMA pipes for the LCS roofline.  Allocates a small output buffer. */
 int famsa_debug_int_pipe_rate(int kind, double *inst_per_s);
 
+/* SM clocks per repetition of one building block of the row update, on one
+ * cluster of cluster_ctas (1, 2, 4, 8 or 16) CTAs of 512 threads, timed by
+ * thread 0 of CTA 0 over 4,096 repetitions: kind 0 the block clamp scan with
+ * order-code keys, 1 the same with cross-multiplied keys, 2 a cluster
+ * barrier, 3 every CTA pushing one clamp into every CTA's shared memory and
+ * a cluster barrier, 4 a dependent load from local shared memory, 5 a
+ * dependent load from the next CTA's shared memory.  Allocates a few KB. */
+int famsa_debug_cluster_probe(int kind, int cluster_ctas, double *cycles);
+
 /* on != 0 (default): families of up to 4,096 points are finalised by one
  * CTA in one launch; 0: every family takes the multi-kernel finalisation.
  * Both give the same outputs.  Returns FAMSA_OK. */

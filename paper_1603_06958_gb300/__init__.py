@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
             "famsa_debug_int_pipe_rate": ([ctypes.c_int, _P], ctypes.c_int),
+            "famsa_debug_cluster_probe": ([ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
             "famsa_debug_set_global_variant": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_fin_small": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_order_code": ([ctypes.c_uint32, ctypes.c_uint32, _P], ctypes.c_int),
@@ -547,6 +548,14 @@ def debug_int_pipe_rate(kind: int) -> float:
     LOP3+IMAD (3) chains over the whole device."""
     out = ctypes.c_double()
     _check(load().famsa_debug_int_pipe_rate(kind, ctypes.byref(out)), "famsa_debug_int_pipe_rate")
+    return out.value
+
+
+def debug_cluster_probe(kind: int, cluster_ctas: int = 16) -> float:
+    """SM clocks per repetition of a row-update building block (see the C header)."""
+    out = ctypes.c_double()
+    _check(load().famsa_debug_cluster_probe(int(kind), int(cluster_ctas), ctypes.byref(out)),
+           "famsa_debug_cluster_probe")
     return out.value
 
 
