@@ -343,8 +343,8 @@ void famsa_free(famsa_family *f);
  *   13 its cluster size, 14..17 kilocycles spent by one thread of the
  *   shared-memory kernel in its phases (14 unused; 15 scans, pointer update
  *   and prefetch; 16 shift re-layout plus the next point's distances;
- *   17 run-merge re-layout), 18 1 when keys used the 32-bit-numerator
- *   packing, 19 run merges done in shared memory, 20 the runs they
+ *   17 run-merge re-layout), 18 1 when keys were exact order codes (every
+ *   length <= 32767), 19 run merges done in shared memory, 20 the runs they
  *   merged (both sides), 21..23 reserved.
  * Returns EINVAL for NULL arguments.
  */
