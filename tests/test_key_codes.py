@@ -82,3 +82,21 @@ def test_code_argument_errors(lib):
     assert lib.famsa_debug_order_code(1, 0, ctypes.byref(out)) == fg.FAMSA_EINVAL
     assert lib.famsa_debug_order_code(1, 32768, ctypes.byref(out)) == fg.FAMSA_EINVAL
     assert lib.famsa_debug_order_code(1, 1, None) == fg.FAMSA_EINVAL
+
+
+def test_code_sweep_over_denominators(lib):
+    # every 7th denominator 1..32767, numerators at and around multiples of
+    # it across the 32-bit range: code = floor(num * 2^30 / den) and decoding
+    # gives the reduced fraction back
+    rng = random.Random(5)
+    for den in range(1, 32768, 7):
+        qmax = (2 ** 32 - 1) // den
+        for q in (0, 1, qmax // 3, qmax // 2, qmax - 1, qmax, rng.randint(0, qmax)):
+            for delta in (0, 1, den - 1):
+                num = q * den + delta
+                if num >= 2 ** 32:
+                    continue
+                code = fg.debug_order_code(num, den)
+                assert code == (num << 30) // den, (num, den)
+                g = math.gcd(num, den)
+                assert fg.debug_code_fraction(code) == (num // g, den // g), (num, den)
