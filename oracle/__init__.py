@@ -11,6 +11,9 @@ Functions and the paper passages they follow (FAMSA, Methods):
 
 * :func:`lcs`, :func:`lcs_pairs`, :func:`lcs_allpairs`, :func:`lcs_rows` --
   LCS length by the textbook DP rule ("Pairwise similarities calculation").
+* :func:`lcs_bitpar`, :func:`lcs_pairs_bitpar` -- the same LCS length by
+  the bit-parallel recurrence the paper applies in stage I, as plain scalar
+  64-bit C; pinned against the DP.
 * :func:`key` -- the exact rational distance indel^2 / LCS used to order
   pairs; indel = |A| + |B| - 2 LCS and similarity = LCS / indel^2 are the
   two displayed equations of the same subsection.
@@ -20,6 +23,9 @@ Functions and the paper passages they follow (FAMSA, Methods):
   pointer representation read off the merges.
 * :func:`slink_definition` -- the pointer representation evaluated from its
   definition via the minimax (single-link ultrametric) closure.
+* :func:`slink_bitpar_range`, :func:`tree_bitpar` -- Sibson's SLINK fed by
+  bit-parallel rows, resumable over ranges of points, for families too large
+  for the DP (the k=400,000 digest).
 * :func:`merges` -- the merge list with the fixed (lambda, index) order.
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against brute
@@ -68,6 +74,12 @@ def _load():
             "oracle_lcs": ([_P, i32, _P, i32], i32),
             "oracle_num_threads": ([], ctypes.c_int),
             "oracle_lcs_pairs": ([_P, _P, i32, _P, _P, i64, _P, ctypes.c_int], ctypes.c_int),
+            "oracle_lcs_bitpar": ([_P, i32, _P, i32], i32),
+            "oracle_lcs_pairs_bitpar": ([_P, _P, i32, _P, _P, i64, _P, ctypes.c_int],
+                                        ctypes.c_int),
+            "oracle_slink_bitpar_range": ([_P, _P, i32, i32, i32, _P, _P, _P, ctypes.c_int],
+                                          ctypes.c_int),
+            "oracle_reduce_keys": ([_P, _P, i64, _P, _P], ctypes.c_int),
             "oracle_lcs_allpairs": ([_P, _P, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_lcs_rows": ([_P, _P, i32, i32, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_slink_matrix": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
@@ -121,6 +133,26 @@ def lcs_pairs(residues, offsets, pa, pb, nthreads: int = 0) -> np.ndarray:
     out = np.empty(len(pa), dtype=np.int32)
     _check(_load().oracle_lcs_pairs(_ptr(res), _ptr(off), k, _ptr(pa), _ptr(pb), len(pa),
                                     _ptr(out), nthreads), "oracle_lcs_pairs")
+    return out
+
+
+def lcs_bitpar(a, b) -> int:
+    """LCS length of two code sequences by the bit-parallel recurrence (A = a is the Peq side)."""
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    b = np.ascontiguousarray(b, dtype=np.uint8)
+    r = _load().oracle_lcs_bitpar(_ptr(a), len(a), _ptr(b), len(b))
+    _check(0 if r >= 0 else r, "oracle_lcs_bitpar")
+    return int(r)
+
+
+def lcs_pairs_bitpar(residues, offsets, pa, pb, nthreads: int = 0) -> np.ndarray:
+    """Bit-parallel LCS of the pairs (pa[t], pb[t]); pa[t] is the Peq side."""
+    res, off, k = _prep(residues, offsets)
+    pa = np.ascontiguousarray(pa, dtype=np.int32)
+    pb = np.ascontiguousarray(pb, dtype=np.int32)
+    out = np.empty(len(pa), dtype=np.int32)
+    _check(_load().oracle_lcs_pairs_bitpar(_ptr(res), _ptr(off), k, _ptr(pa), _ptr(pb), len(pa),
+                                           _ptr(out), nthreads), "oracle_lcs_pairs_bitpar")
     return out
 
 
@@ -194,6 +226,53 @@ def slink_streamed(residues, offsets, nthreads: int = 0):
     _check(_load().oracle_slink_streamed(_ptr(res), _ptr(off), k, _ptr(pi), _ptr(ln), _ptr(ld),
                                          nthreads), "oracle_slink_streamed")
     return pi, ln, ld
+
+
+def slink_state(k: int):
+    """Empty pointer state for :func:`slink_bitpar_range`: pi, lambda num, lambda den (unreduced)."""
+    return {"pi": np.zeros(k, dtype=np.int32), "lam_num": np.zeros(k, dtype=np.uint64),
+            "lam_den": np.zeros(k, dtype=np.uint32)}
+
+
+def slink_bitpar_range(residues, offsets, state, n0: int, n1: int, nthreads: int = 0):
+    """Insert points n0..n1-1 into ``state`` (from :func:`slink_state`), rows by bit-parallel LCS."""
+    res, off, k = _prep(residues, offsets)
+    for name, dt in (("pi", np.int32), ("lam_num", np.uint64), ("lam_den", np.uint32)):
+        a = state[name]
+        if a.dtype != dt or a.shape != (k,) or not a.flags.c_contiguous:
+            raise ValueError("bad state array " + name)
+    _check(_load().oracle_slink_bitpar_range(_ptr(res), _ptr(off), k, n0, n1, _ptr(state["pi"]),
+                                             _ptr(state["lam_num"]), _ptr(state["lam_den"]),
+                                             nthreads), "oracle_slink_bitpar_range")
+    return state
+
+
+def reduce_keys(num, den):
+    """Keys num/den in lowest terms (+inf = 1/0, zero = 0/1)."""
+    num = np.ascontiguousarray(num, dtype=np.uint64)
+    den = np.ascontiguousarray(den, dtype=np.uint32)
+    rn = np.empty_like(num)
+    rd = np.empty_like(den)
+    _check(_load().oracle_reduce_keys(_ptr(num), _ptr(den), len(num), _ptr(rn), _ptr(rd)),
+           "oracle_reduce_keys")
+    return rn, rd
+
+
+def tree_from_state(state):
+    """Full tree result (pi, reduced lambda, merge list) from a completed pointer state."""
+    pi = state["pi"].copy()
+    ln, ld = reduce_keys(state["lam_num"], state["lam_den"])
+    pairs, hn, hd, sz = merges(pi, ln, ld)
+    return {"pi": pi, "lambda_num": ln, "lambda_den": ld, "merges": pairs, "h_num": hn,
+            "h_den": hd, "sizes": sz}
+
+
+def tree_bitpar(residues, offsets, nthreads: int = 0):
+    """Like :func:`tree`, but the SLINK rows come from the bit-parallel LCS."""
+    res, off, k = _prep(residues, offsets)
+    st = slink_state(k)
+    slink_bitpar_range(res, off, st, 0, k, nthreads)
+    return tree_from_state(st)
 
 
 def slink_naive(lcs_tri, lens):

@@ -12,6 +12,11 @@
  *     perfectly matching columns, computable by a straightforward DP rule).
  *     Matching is literal code equality (ambiguity codes match only
  *     themselves).
+ *   - LCS length a second, independent way: the bit-parallel recurrence the
+ *     paper applies in stage I (same subsection), written as plain scalar
+ *     64-bit C with the carry rippled word by word.  It exists so that trees
+ *     of families far too large for the DP can still be computed by the
+ *     oracle; it is pinned against the DP and never against the GPU.
  *   - indel(A,B) = |A| + |B| - 2 LCS(A,B) and similarity = LCS / indel^2
  *     (the two displayed equations of that subsection).  The tree is keyed on
  *     the exact rational distance indel^2 / LCS, a strictly decreasing
@@ -138,6 +143,113 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* ------------------------------------------------------------ LCS, bit-parallel */
+/*
+ * The bit-parallel form of the same LCS length (FAMSA Methods, "Pairwise
+ * similarities calculation": the LCS is computed with the bit-parallel
+ * algorithm it cites, 64 DP cells per machine word).  Position p of A is bit
+ * p % 64 of word p / 64 of a vector of W = ceil(|A| / 64) words.
+ * Peq[c] has bit p set exactly when A[p] == c (any byte value c: matching is
+ * literal equality).  V starts with every bit set; each symbol c of B, in
+ * order, replaces V by
+ *     V' = (V + (V & Peq[c])) | (V & ~Peq[c]),
+ * where + adds the two W-word numbers, word 0 least significant, the carry
+ * out of word w going into word w + 1 and the carry out of the last word
+ * dropped.  The LCS length is the number of zero bits of V among the |A|
+ * positions.  Bits above |A| in the last word stay one: Peq is zero there,
+ * so both terms of the OR keep them set.
+ */
+#define BP_CODES 256
+
+static void bp_peq(const uint8_t *a, int32_t la, int32_t W, uint64_t *peq /* [BP_CODES][W] */) {
+  memset(peq, 0, sizeof(uint64_t) * (size_t)BP_CODES * (size_t)W);
+  for (int32_t p = 0; p < la; ++p) peq[(size_t)a[p] * W + p / 64] |= (uint64_t)1 << (p % 64);
+}
+
+/* the recurrence for W words; V is the caller's W-word scratch */
+static inline __attribute__((always_inline)) int32_t
+bp_lcs_body(const uint64_t *peq, const int32_t W, int32_t la, const uint8_t *b, int32_t lb,
+            uint64_t *V) {
+  for (int32_t w = 0; w < W; ++w) V[w] = ~(uint64_t)0;
+  for (int32_t i = 0; i < lb; ++i) {
+    const uint64_t *P = peq + (size_t)b[i] * W;
+    unsigned long long carry = 0;
+    for (int32_t w = 0; w < W; ++w) {
+      unsigned long long v = V[w], s, t;
+      unsigned c1 = __builtin_uaddll_overflow(v, v & P[w], &s); /* V + (V & Peq[c]) */
+      unsigned c2 = __builtin_uaddll_overflow(s, carry, &t);    /* + carry from word w - 1 */
+      carry = c1 | c2;                                          /* at most one is set */
+      V[w] = t | (v & ~P[w]);                                   /* | (V & ~Peq[c]) */
+    }
+  }
+  int32_t ones = 0;
+  for (int32_t p = 0; p < la; ++p) ones += (int32_t)((V[p / 64] >> (p % 64)) & 1);
+  return la - ones;
+}
+
+/* The same function; small widths are spelled out as constants only so that the
+   compiler keeps V in registers (about 1.5x faster on the host, same arithmetic). */
+static int32_t bp_lcs(const uint64_t *peq, int32_t W, int32_t la, const uint8_t *b, int32_t lb,
+                      uint64_t *V) {
+  uint64_t R[8];
+  switch (W) {
+    case 1: return bp_lcs_body(peq, 1, la, b, lb, R);
+    case 2: return bp_lcs_body(peq, 2, la, b, lb, R);
+    case 3: return bp_lcs_body(peq, 3, la, b, lb, R);
+    case 4: return bp_lcs_body(peq, 4, la, b, lb, R);
+    case 5: return bp_lcs_body(peq, 5, la, b, lb, R);
+    case 6: return bp_lcs_body(peq, 6, la, b, lb, R);
+    case 7: return bp_lcs_body(peq, 7, la, b, lb, R);
+    case 8: return bp_lcs_body(peq, 8, la, b, lb, R);
+    default: return bp_lcs_body(peq, W, la, b, lb, V);
+  }
+}
+
+static int32_t words_of(int32_t len) { return len > 0 ? (len + 63) / 64 : 1; }
+
+int32_t oracle_lcs_bitpar(const uint8_t *a, int32_t la, const uint8_t *b, int32_t lb) {
+  if (la < 0 || lb < 0) return -1;
+  int32_t W = words_of(la);
+  uint64_t *peq = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)BP_CODES * (size_t)W);
+  uint64_t *V = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+  if (!peq || !V) { free(peq); free(V); return -2; }
+  bp_peq(a, la, W, peq);
+  int32_t r = bp_lcs(peq, W, la, b, lb, V);
+  free(peq);
+  free(V);
+  return r;
+}
+
+/* bit-parallel LCS for an explicit list of pairs; A = pa[t] is the Peq side */
+int oracle_lcs_pairs_bitpar(const uint8_t *res, const int64_t *off, int32_t k, const int32_t *pa,
+                            const int32_t *pb, int64_t npairs, int32_t *out, int nthreads) {
+  if (k < 1 || npairs < 0) return -1;
+  set_threads(nthreads);
+  int32_t W = words_of(max_len(off, k));
+  int bad = 0;
+#pragma omp parallel
+  {
+    uint64_t *peq = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)BP_CODES * (size_t)W);
+    uint64_t *V = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+    if (!peq || !V) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t t = 0; t < npairs; ++t) {
+      if (!peq || !V) continue;
+      int32_t i = pa[t], j = pb[t];
+      int32_t la = (int32_t)(off[i + 1] - off[i]);
+      int32_t wa = words_of(la);
+      bp_peq(res + off[i], la, wa, peq);
+      out[t] = bp_lcs(peq, wa, la, res + off[j], (int32_t)(off[j + 1] - off[j]), V);
+    }
+    free(peq);
+    free(V);
+  }
+  return bad ? -2 : 0;
+}
+
 /* LCS for an explicit list of pairs (pa[t], pb[t]) */
 int oracle_lcs_pairs(const uint8_t *res, const int64_t *off, int32_t k, const int32_t *pa,
                      const int32_t *pb, int64_t npairs, int32_t *out, int nthreads) {
@@ -242,6 +354,24 @@ static void write_lambda(const okey *lam, int32_t k, uint64_t *lnum, uint32_t *l
  */
 typedef void (*row_fn)(void *ctx, int32_t n, okey *M);
 
+/* one insertion: point n joins points 0..n-1, whose distances to it are M[0..n-1] */
+static void slink_insert(int32_t n, int32_t *pi, okey *lam, okey *M) {
+  pi[n] = n;
+  lam[n] = KEY_INF;
+  for (int32_t j = 0; j < n; ++j) {
+    int32_t p = pi[j];
+    if (!key_lt(lam[j], M[j])) {
+      M[p] = key_min(M[p], lam[j]);
+      lam[j] = M[j];
+      pi[j] = n;
+    } else {
+      M[p] = key_min(M[p], M[j]);
+    }
+  }
+  for (int32_t j = 0; j < n; ++j)
+    if (!key_lt(lam[j], lam[pi[j]])) pi[j] = n;
+}
+
 static int slink_core(int32_t k, row_fn fn, void *ctx, int32_t *pi, uint64_t *lnum,
                       uint32_t *lden) {
   okey *lam = (okey *)malloc(sizeof(okey) * (size_t)k);
@@ -250,21 +380,8 @@ static int slink_core(int32_t k, row_fn fn, void *ctx, int32_t *pi, uint64_t *ln
   pi[0] = 0;
   lam[0] = KEY_INF;
   for (int32_t n = 1; n < k; ++n) {
-    pi[n] = n;
-    lam[n] = KEY_INF;
     fn(ctx, n, M);
-    for (int32_t j = 0; j < n; ++j) {
-      int32_t p = pi[j];
-      if (!key_lt(lam[j], M[j])) {
-        M[p] = key_min(M[p], lam[j]);
-        lam[j] = M[j];
-        pi[j] = n;
-      } else {
-        M[p] = key_min(M[p], M[j]);
-      }
-    }
-    for (int32_t j = 0; j < n; ++j)
-      if (!key_lt(lam[j], lam[pi[j]])) pi[j] = n;
+    slink_insert(n, pi, lam, M);
   }
   write_lambda(lam, k, lnum, lden);
   free(lam);
@@ -326,6 +443,78 @@ int oracle_slink_streamed(const uint8_t *res, const int64_t *off, int32_t k, int
   for (int t = 0; t < nt; ++t) free(rows[t]);
   free(rows);
   return rc;
+}
+
+/*
+ * Streamed SLINK whose rows come from the bit-parallel LCS.  Row n builds the
+ * Peq table of sequence n once and runs every earlier sequence j < n through
+ * it.  The pointer state is passed in and out (pi, and lambda as unreduced
+ * num/den with den 0 = +inf) so that a run over a very large family can be
+ * split into ranges of points [n0, n1) and saved in between; n0 == 0 starts
+ * from the empty state.  Inserting the points of [0, k) in ranges gives the
+ * same state as one call, since SLINK inserts one point at a time anyway.
+ */
+typedef struct {
+  const uint8_t *res; const int64_t *off; uint64_t *peq; uint64_t **V;
+} bp_ctx;
+static void bp_row(void *c, int32_t n, okey *M) {
+  bp_ctx *t = (bp_ctx *)c;
+  int32_t la = (int32_t)(t->off[n + 1] - t->off[n]);
+  int32_t wa = words_of(la);
+  bp_peq(t->res + t->off[n], la, wa, t->peq);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t j = 0; j < n; ++j) {
+#ifdef _OPENMP
+    uint64_t *V = t->V[omp_get_thread_num()];
+#else
+    uint64_t *V = t->V[0];
+#endif
+    int32_t lb = (int32_t)(t->off[j + 1] - t->off[j]);
+    int32_t L = bp_lcs(t->peq, wa, la, t->res + t->off[j], lb, V);
+    M[j] = key_from_lcs(L, lb, la);
+  }
+}
+
+int oracle_slink_bitpar_range(const uint8_t *res, const int64_t *off, int32_t k, int32_t n0,
+                              int32_t n1, int32_t *pi, uint64_t *lam_num, uint32_t *lam_den,
+                              int nthreads) {
+  if (k < 1 || n0 < 0 || n1 > k || n0 > n1) return -1;
+  set_threads(nthreads);
+  int nt = oracle_num_threads();
+  int32_t W = words_of(max_len(off, k));
+  okey *lam = (okey *)malloc(sizeof(okey) * (size_t)k);
+  okey *M = (okey *)malloc(sizeof(okey) * (size_t)k);
+  uint64_t *peq = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)BP_CODES * (size_t)W);
+  uint64_t **V = (uint64_t **)calloc((size_t)nt, sizeof(uint64_t *));
+  int rc = (lam && M && peq && V) ? 0 : -2;
+  for (int t = 0; rc == 0 && t < nt; ++t) {
+    V[t] = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+    if (!V[t]) rc = -2;
+  }
+  if (rc == 0) {
+    for (int32_t j = 0; j < n0; ++j) { lam[j].num = lam_num[j]; lam[j].den = lam_den[j]; }
+    bp_ctx c = {res, off, peq, V};
+    for (int32_t n = n0; n < n1; ++n) {
+      if (n == 0) { pi[0] = 0; lam[0] = KEY_INF; continue; }
+      bp_row(&c, n, M);
+      slink_insert(n, pi, lam, M);
+    }
+    for (int32_t j = 0; j < n1; ++j) { lam_num[j] = lam[j].num; lam_den[j] = lam[j].den; }
+  }
+  if (V) for (int t = 0; t < nt; ++t) free(V[t]);
+  free(V); free(peq); free(lam); free(M);
+  return rc;
+}
+
+/* reduce keys to lowest terms (+inf = 1/0, zero = 0/1), as the tree functions output them */
+int oracle_reduce_keys(const uint64_t *num, const uint32_t *den, int64_t n, uint64_t *rnum,
+                       uint32_t *rden) {
+  if (n < 0) return -1;
+  for (int64_t t = 0; t < n; ++t) {
+    okey q = {num[t], den[t]};
+    key_reduce(q, &rnum[t], &rden[t]);
+  }
+  return 0;
 }
 
 /*
