@@ -726,7 +726,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0,
                     help="--impl reference: host seconds of oracle work per step")
-    ap.add_argument("--update-path", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--update-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="row-update kernel: 0 automatic, 1 cluster shared memory, 2 global memory "
                          "(profiling; the default picks by family size)")
     ap.add_argument("--global-variant", type=int, default=-1, choices=[-1, 0, 1],

@@ -27,18 +27,27 @@ int famsa_debug_set_tpp_max_w(int w);
  * Results are identical for every size.  Returns FAMSA_EINVAL otherwise. */
 int famsa_debug_set_cluster(int ctas);
 
-/* Select the row-update kernel: 0 automatic (cluster shared memory when the
- * family fits, else global memory), 1 cluster shared memory (the tree call
- * returns FAMSA_EINVAL when the family does not fit), 2 global memory.
- * Results are identical.  Returns FAMSA_EINVAL outside 0..2. */
+/* Select the row update: 0 automatic (3 when every length is <= 32767,
+ * else the insertion kernels: cluster shared memory when the family fits,
+ * else global memory), 1 insertion in cluster shared memory (the tree call
+ * returns FAMSA_EINVAL when the family does not fit), 2 insertion in global
+ * memory, 3 minimum-spanning-tree rebuild per row block (FAMSA_EINVAL from
+ * the tree call when a length is above 32767).  Results are identical.
+ * Returns FAMSA_EINVAL outside 0..3. */
 int famsa_debug_set_update_path(int path);
 
-/* The pointer representation produced by the row updates of the last
- * famsa_slink_tree call on f, in insertion labels: points are inserted in
+/* Rows per row block of famsa_slink_tree (0 = automatic; otherwise 1 to
+ * 2048).  Small blocks make many blocks out of a small family.  Results are
+ * identical.  Returns FAMSA_EINVAL outside 0..2048. */
+int famsa_debug_set_row_block(int rows);
+
+/* The pointer representation produced by the insertion row updates (paths
+ * 1 and 2) of the last famsa_slink_tree call on f, in insertion labels: points are inserted in
  * the family's (length, index) order; perm[j] is the caller's label of the
  * j-th inserted point, pi[j] / (lam_num[j], lam_den[j]) its pointer and
  * height (reduced; +inf = (1, 0)).  Host arrays of k entries; any may be
- * NULL.  Returns FAMSA_EINVAL when no tree was built on f. */
+ * NULL.  Returns FAMSA_EINVAL when no tree was built on f by an insertion
+ * path. */
 int famsa_debug_insertion_state(const famsa_family *f, int32_t *perm, int32_t *pi,
                                 uint64_t *lam_num, uint32_t *lam_den);
 

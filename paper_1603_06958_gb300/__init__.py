@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_tpp_max_w": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_cluster": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_serial": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
@@ -513,7 +514,7 @@ def debug_set_tpp_max_w(w: int):
 
 
 def debug_set_update_path(path: int):
-    """0 automatic, 1 cluster shared-memory row update, 2 global-memory row update."""
+    """0 automatic, 1/2 insertion row update (cluster shared / global memory), 3 tree rebuild."""
     _check(load().famsa_debug_set_update_path(path), "famsa_debug_set_update_path")
 
 
@@ -526,6 +527,11 @@ def debug_insertion_state(fam: Family) -> dict:
                                                             ("perm", "pi", "lambda_num", "lambda_den")]),
            "famsa_debug_insertion_state")
     return out
+
+
+def debug_set_row_block(rows: int):
+    """Rows per row block of the tree build (0 = automatic)."""
+    _check(load().famsa_debug_set_row_block(rows), "famsa_debug_set_row_block")
 
 
 def debug_set_update_threads(threads: int):

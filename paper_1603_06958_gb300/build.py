@@ -16,9 +16,9 @@ LIB = os.path.join(HERE, "libfamsa_gpu.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu", "lcs_tpp_d.cu",
-           "lcs_wpp.cu", "slink.cu", "slink_global.cu", "slink_smem.cu", "finalize.cu",
+           "lcs_wpp.cu", "slink.cu", "slink_global.cu", "slink_smem.cu", "slink_msf.cu", "finalize.cu",
            "noalloc.cu", "int_peak.cu", "batch.cu", "server.cu", "cluster_probe.cu"]
-HEADERS = ["famsa_internal.cuh", "lcs_kernels.cuh", "lcs_step.inc", "slink_common.cuh",
+HEADERS = ["famsa_internal.cuh", "lcs_kernels.cuh", "lcs_step.inc", "slink_common.cuh", "slink_msf.cuh",
            "slink_merge.cuh", os.path.join(ROOT, "include", "famsa_gpu_debug.h"),
            os.path.join(ROOT, "include", "famsa_gpu.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

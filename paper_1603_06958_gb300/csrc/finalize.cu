@@ -119,25 +119,6 @@ struct ByParent {
   }
 };
 
-// one element of a bottom-up merge pass on an index array under a strict total order
-template <class Cmp>
-__device__ __forceinline__ void msort_at(int32_t i, const int32_t *in, int32_t *out, int32_t n, int32_t width,
-                                         Cmp cmp) {
-  int64_t run = i / width;
-  int64_t start = run * width;
-  int64_t pair_start = (run & ~1LL) * width;
-  int64_t pstart = (run ^ 1) * width;
-  int32_t x = in[i];
-  if (pstart >= n) { out[i] = x; return; }
-  int64_t pend = pstart + width < n ? pstart + width : (int64_t)n;
-  int64_t lo = pstart, hi = pend;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (cmp(in[mid], x)) lo = mid + 1; else hi = mid;
-  }
-  out[pair_start + (i - start) + (lo - pstart)] = x;
-}
-
 __device__ __forceinline__ void fin_merges_at(int32_t s, const int32_t *sorder, const int32_t *pi,
                                               const uint64_t *lam, const int32_t *rank,
                                               const int32_t *sub_lo, const int32_t *sub_hi,

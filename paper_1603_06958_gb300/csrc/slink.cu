@@ -15,12 +15,16 @@
 #include <algorithm>
 #include <vector>
 
-#include "slink_common.cuh"
+#include "slink_msf.cuh"
 
 namespace famsa {
 
 static int g_force_cluster = 0;
-static int g_update_path = 0;  // 0 automatic, 1 shared-memory kernel, 2 global-memory kernel
+// 0 automatic, 1 shared-memory insertion kernel, 2 global-memory insertion
+// kernel, 3 minimum-spanning-tree rebuild per row block (automatic whenever
+// every length is <= 32767; the insertion kernels take longer sequences)
+static int g_update_path = 0;
+static int g_row_block = 0;  // rows per row block (0 automatic)
 static int g_serial = 0;       // 1: no overlap of LCS and row update (timing studies)
 
 struct Scratch {
@@ -49,18 +53,21 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
   for (int i = 0; i < kStatsLen; ++i) f->stats[i] = 0;
   cudaError_t err = cudaSuccess;
 
-  // which row-update kernel, and its cluster size
+  // which row update, and the insertion kernels' cluster size
+  const bool narrow = f->max_len <= 32767;
   int path = g_update_path, cl = 0;
-  if (path != 2) {
+  if (path == 0 && narrow) path = 3;
+  if (path == 3 && !narrow) return FAMSA_EINVAL;
+  const bool msf = path == 3;
+  if (!msf && path != 2) {
     cl = g_force_cluster ? smem_cluster_for(k, g_force_cluster) : smem_cluster_latency(k);
     if (cl > max_cluster_global()) cl = 0;
     if (cl == 0 && path == 1) return FAMSA_EINVAL;
     path = cl ? 1 : 2;
   }
   if (path == 2) cl = g_force_cluster ? g_force_cluster : max_cluster_global();
-  // both row-update kernels compare exact order codes floor(num * 2^30 / den)
-  // when every indel^2 fits in 32 bits and every LCS in 15 (all lengths <= 32767)
-  const bool narrow = f->max_len <= 32767;
+  // every row update compares exact order codes floor(num * 2^30 / den) when
+  // every indel^2 fits in 32 bits and every LCS in 15 (all lengths <= 32767)
 
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
@@ -94,34 +101,71 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     CKE(cudaEventCreateWithFlags(&upd_done[i], cudaEventDisableTiming));
   }
   {
-    SlinkState S;
+    SlinkState S = {};
+    MsfState M = {};
     const size_t kp = (size_t)k + 1;
-    for (int i = 0; i < 2; ++i) {
-      S.ord[i] = sc.get<int32_t>(kp);
-      S.olen[i] = sc.get<int32_t>(kp);
-      S.gap[i] = sc.get<uint64_t>(kp);
-      S.lam[i] = sc.get<uint64_t>(kp);
-      S.pi[i] = sc.get<int32_t>(kp);
-      S.mD[i] = sc.get<uint64_t>(kp);
-      S.mOrd[i] = sc.get<int32_t>(kp);
-      S.mLen[i] = sc.get<int32_t>(kp);
-      S.mOld[i] = sc.get<int32_t>(kp);
-      S.mLam[i] = sc.get<uint64_t>(kp);
-      S.mPi[i] = sc.get<int32_t>(kp);
-      S.mRaw[i] = sc.get<int32_t>(kp);
+    if (!msf) {
+      for (int i = 0; i < 2; ++i) {
+        S.ord[i] = sc.get<int32_t>(kp);
+        S.olen[i] = sc.get<int32_t>(kp);
+        S.gap[i] = sc.get<uint64_t>(kp);
+        S.lam[i] = sc.get<uint64_t>(kp);
+        S.pi[i] = sc.get<int32_t>(kp);
+        S.mD[i] = sc.get<uint64_t>(kp);
+        S.mOrd[i] = sc.get<int32_t>(kp);
+        S.mLen[i] = sc.get<int32_t>(kp);
+        S.mOld[i] = sc.get<int32_t>(kp);
+        S.mLam[i] = sc.get<uint64_t>(kp);
+        S.mPi[i] = sc.get<int32_t>(kp);
+        S.mRaw[i] = sc.get<int32_t>(kp);
+      }
+      S.D = sc.get<uint64_t>(kp);
+      S.mGap = sc.get<uint64_t>(kp);
+      S.runsA = sc.get<int32_t>(kp);
+      S.runsB = sc.get<int32_t>(kp);
+      S.ctl = sc.get<uint64_t>(kCtlWords);
     }
-    S.D = sc.get<uint64_t>(kp);
-    S.mGap = sc.get<uint64_t>(kp);
-    S.runsA = sc.get<int32_t>(kp);
-    S.runsB = sc.get<int32_t>(kp);
-    S.ctl = sc.get<uint64_t>(kCtlWords);
     S.slen = f->d_slen;
-    // row blocks: about 128 MB of 16-bit LCS values per buffer
-    int32_t B = (int32_t)std::min<int64_t>(std::max<int64_t>((int64_t)(1 << 26) / std::max(k, 1), 64), 2048);
+    // row blocks: about 128 MB of 16-bit LCS values per buffer for the
+    // insertion kernels; the tree rebuild costs a few passes over its block,
+    // so it takes blocks up to 8x larger (fewer, larger launches)
+    const int64_t budget = msf ? (int64_t)1 << 29 : (int64_t)1 << 26;
+    int32_t B = (int32_t)std::min<int64_t>(std::max<int64_t>(budget / std::max(k, 1), 64), 2048);
+    if (g_row_block) B = g_row_block;
     B = std::min(B, std::max(k - 1, 1));
     const int64_t ld = (k + 1) & ~1;  // even: rows start on 4-byte boundaries
     uint16_t *rowbuf[kRowBuffers];
     for (int i = 0; i < kRowBuffers; ++i) rowbuf[i] = sc.get<uint16_t>((size_t)B * ld);
+    int32_t *msf_ord = nullptr, *msf_ia = nullptr, *msf_ib = nullptr, *msf_work = nullptr;
+    uint64_t *msf_gap = nullptr, *msf_gafter = nullptr;
+    if (msf) {
+      M.comp = sc.get<int32_t>(kp);
+      M.par = sc.get<int32_t>(kp);
+      M.rkey = sc.get<uint64_t>((size_t)B);
+      M.roth = sc.get<int32_t>((size_t)B);
+      M.ckey = sc.get<uint64_t>(kp);
+      M.coth = sc.get<int32_t>(kp);
+      M.vkey = sc.get<uint64_t>(kp);
+      M.vab = sc.get<uint64_t>(kp);
+      M.bkey = sc.get<uint64_t>(kp);
+      M.bab = sc.get<uint64_t>(kp);
+      M.mkey = sc.get<uint64_t>(kp);
+      M.ma = sc.get<int32_t>(kp);
+      M.mb = sc.get<int32_t>(kp);
+      M.nkey = sc.get<uint64_t>(kp);
+      M.na = sc.get<int32_t>(kp);
+      M.nb = sc.get<int32_t>(kp);
+      M.cap = (int32_t)kp;
+      M.ctl = sc.get<int32_t>(kMsfCtlWords);
+      M.keys = sc.get<uint64_t>((size_t)B * ld);
+      M.slen = f->d_slen;
+      msf_ord = sc.get<int32_t>(kp);
+      msf_ia = sc.get<int32_t>(kp);
+      msf_ib = sc.get<int32_t>(kp);
+      msf_work = sc.get<int32_t>(8 * kp);
+      msf_gap = sc.get<uint64_t>(kp);
+      msf_gafter = sc.get<uint64_t>(kp);
+    }
     std::vector<int32_t> h_iota(k), h_w(k);
     for (int32_t s = 0; s < k; ++s) { h_iota[s] = s; h_w[s] = (f->h_slen[s] + 63) / 64; }
     int32_t *d_iota = sc.get<int32_t>(k);
@@ -141,8 +185,10 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     FB.sz = sc.get<int64_t>(k); FB.szpre = sc.get<int64_t>(k); FB.tot = sc.get<int64_t>(2);
     if (sc.err != cudaSuccess) { err = sc.err; goto done; }
     CKE(cudaMemcpyAsync(d_iota, h_iota.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
-    CKE(cudaMemsetAsync(S.ctl, 0, sizeof(uint64_t) * kCtlWords, st));
-    {
+    if (msf) {
+      CKE(cudaMemsetAsync(M.ctl, 0, sizeof(int32_t) * kMsfCtlWords, st));
+    } else {
+      CKE(cudaMemsetAsync(S.ctl, 0, sizeof(uint64_t) * kCtlWords, st));
       // the layout of one point (point 0): buffer 1
       std::vector<int32_t> z1 = {0};
       std::vector<uint64_t> inf1 = {narrow ? KeysNarrow::kInf : KeysWide::kInf};
@@ -168,9 +214,16 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     int32_t blk = 0;
     // the first block is an eighth of the others: the row update can start
     // once its few, short rows are done
-    const int32_t B0 = std::min(B, std::max(B / 8, 64));  // the buffers hold B rows
+    const int32_t B0 = g_row_block ? B : std::min(B, std::max(B / 8, 64));  // the buffers hold B rows
     for (int32_t r0 = 1, r1 = 0; r0 < k; r0 = r1, ++blk) {
-      r1 = std::min(r0 + (blk == 0 ? B0 : B), k);
+      {
+        // the last block is a quarter of the others, so that little row
+        // update work is left once the last LCS block is done
+        int32_t take = blk == 0 ? B0 : B;
+        const int32_t rem = k - r0, tail_rows = std::max(B / 4, 1);
+        if (msf && !g_row_block && rem > tail_rows && rem <= take + tail_rows) take = rem - tail_rows;
+        r1 = std::min(r0 + take, k);
+      }
       const int buf = blk % kRowBuffers;
       if (blk >= kRowBuffers) CKE(cudaStreamWaitEvent(sA, upd_done[buf], 0));
       if (g_serial && blk >= 1) CKE(cudaStreamWaitEvent(sA, upd_done[(blk - 1) % kRowBuffers], 0));
@@ -201,9 +254,13 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       CKE(cudaEventRecord(lcs_done[buf], sA));
       CKE(cudaStreamWaitEvent(sB, lcs_done[buf], 0));
       CKE(timing_event(sB));
-      if (path == 1) CKE(launch_slink_smem(S, rowbuf[buf], ld, r0, r1, cl, k, narrow, sB));
-      else CKE(launch_slink_global(S, rowbuf[buf], ld, r0, r1, cl, narrow, sB));
-      ++launches;
+      if (msf) {
+        CKE(launch_msf_block(M, rowbuf[buf], ld, r0, r1, r0 - 1, sB, &launches));
+      } else {
+        if (path == 1) CKE(launch_slink_smem(S, rowbuf[buf], ld, r0, r1, cl, k, narrow, sB));
+        else CKE(launch_slink_global(S, rowbuf[buf], ld, r0, r1, cl, narrow, sB));
+        ++launches;
+      }
       CKE(timing_event(sB));
       CKE(cudaEventRecord(upd_done[buf], sB));
     }
@@ -211,8 +268,12 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     CKE(timing_event(sB));
     // (the streamed lambda is widened for the debug export; the finalisation
     // widens the gaps itself)
-    if (narrow) CKE(widen_keys(S.lam[k & 1], k, sB));
-    if (k >= 2) {
+    if (narrow && !msf) CKE(widen_keys(S.lam[k & 1], k, sB));
+    if (k >= 2 && msf) {
+      // the finished tree -> a dendrogram leaf order and its gaps
+      CKE(launch_msf_leaf_order(M, k, msf_ord, msf_gap, msf_ia, msf_ib, msf_work, msf_gafter, sB, &launches));
+      CKE(launch_finalize(msf_ord, msf_gap, f->d_perm, k, FB, sB, &launches, true));
+    } else if (k >= 2) {
       CKE(launch_finalize(S.ord[k & 1], S.gap[k & 1], f->d_perm, k, FB, sB, &launches, narrow));
     } else {
       std::vector<int32_t> z = {0};
@@ -237,7 +298,18 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
         if (sizes_out) CKE(cudaMemcpyAsync(sizes_out, FB.sizes, sizeof(int32_t) * (k - 1), kind, sB));
       }
     }
-    {
+    if (msf) {
+      int32_t mctl[kMsfCtlWords] = {0};
+      CKE(cudaMemcpyAsync(mctl, M.ctl, sizeof(mctl), cudaMemcpyDeviceToHost, sB));
+      CKE(cudaEventRecord(ev_end, sB));
+      CKE(cudaStreamWaitEvent(st, ev_end, 0));
+      CKE(cudaEventSynchronize(ev_end));
+      f->stats[18] = 1;
+      f->dbg_state.clear();  // no insertion state on this path
+      // a tree that did not come out with k - 1 edges, or a join of two
+      // points already joined, is an internal error
+      if (mctl[kMsfErr]) rc = FAMSA_ECUDA;
+    } else {
       // the insertion-label pointer representation (debug export) and counters
       std::vector<int32_t> ordh(k), pih(k);
       std::vector<uint64_t> lamh(k);
@@ -333,8 +405,14 @@ extern "C" int famsa_debug_sub_kcycles(const famsa_family *fh, int64_t *out16) {
   return FAMSA_OK;
 }
 
+extern "C" int famsa_debug_set_row_block(int rows) {
+  if (rows < 0 || rows > 2048) return FAMSA_EINVAL;
+  famsa::g_row_block = rows;
+  return FAMSA_OK;
+}
+
 extern "C" int famsa_debug_set_update_path(int path) {
-  if (path < 0 || path > 2) return FAMSA_EINVAL;
+  if (path < 0 || path > 3) return FAMSA_EINVAL;
   famsa::g_update_path = path;
   return FAMSA_OK;
 }

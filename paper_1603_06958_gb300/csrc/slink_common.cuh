@@ -293,6 +293,25 @@ __device__ __forceinline__ int32_t merge_count(const uint64_t *key, int32_t sbas
   return lo - ps;
 }
 
+// one element of a bottom-up merge pass on an index array under a strict total order
+template <class Cmp>
+__device__ __forceinline__ void msort_at(int32_t i, const int32_t *in, int32_t *out, int32_t n, int32_t width,
+                                         Cmp cmp) {
+  int64_t run = i / width;
+  int64_t start = run * width;
+  int64_t pair_start = (run & ~1LL) * width;
+  int64_t pstart = (run ^ 1) * width;
+  int32_t x = in[i];
+  if (pstart >= n) { out[i] = x; return; }
+  int64_t pend = pstart + width < n ? pstart + width : (int64_t)n;
+  int64_t lo = pstart, hi = pend;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (cmp(in[mid], x)) lo = mid + 1; else hi = mid;
+  }
+  out[pair_start + (i - start) + (lo - pstart)] = x;
+}
+
 // Buffers for the finalisation (all device, caller-owned)
 // Arguments of the cluster shared-memory row update: insert points r0..r1-1,
 // whose similarity rows are rowbuf[(n - r0) * ld ..].

@@ -1,7 +1,10 @@
 """Scale recipe (k=400,000 family, 25-letter alphabet with X/B/Z ambiguity codes).
 
 A k=2,500 family from the same recipe is checked exactly against the oracle
-on both row-update kernels.  At the full k=400,000 (global-memory row update,
+on every row update.  Prefixes of the k=400,000 family (its first n
+sequences) are checked bit-exactly against oracle tree digests stored by
+tests/golden/make_scale_golden.py, whose SLINK runs on the oracle's own
+bit-parallel LCS.  At the full k=400,000 (global-memory row update,
 about 8e10 pairs streamed in row blocks), LCS rows sampled from the start, the
 middle and the end are checked against the oracle's DP, and the tree against
 properties that hold at any size:
@@ -11,6 +14,10 @@ properties that hold at any size:
     single-link distance never exceeds the direct one;
   * merge heights non-decreasing, ids and sizes consistent, one final cluster.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -40,7 +47,7 @@ def test_scale_recipe_family_exact_both_paths(fg):
     res, off = synth.scale400k(2, k=2500)
     assert int(res.max()) >= 20  # ambiguity codes present
     want = oracle.tree(res, off)
-    for path in (1, 2):
+    for path in (1, 2, 3):
         fg.debug_set_update_path(path)
         try:
             fam = fg.pack_peq(res, off)
@@ -76,7 +83,7 @@ def oracle_rows(full):
 def test_scale400k_sampled_rows_against_oracle(fg, full, oracle_rows):
     res, off, fam, _, st = full
     k = len(off) - 1
-    assert k == 400000 and st["update_path"] == 2 and st["pairs"] == k * (k - 1) // 2
+    assert k == 400000 and st["update_path"] == 3 and st["pairs"] == k * (k - 1) // 2
     for r in SAMPLED_ROWS:
         got = np.asarray(fg.lcs_rows(fam, r, r + 1))
         assert np.array_equal(got, oracle_rows[r]), r
@@ -125,3 +132,37 @@ def test_scale400k_tree_properties(fg, full, oracle_rows):
         used[a] = used[b] = True
         size[k + tt] = size[a] + size[b]
     assert np.array_equal(size[k:], sizes) and sizes[-1] == k
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_trees.json")
+PREFIX = "scale400k_seed1_prefix"
+
+
+def _digest(t):
+    h1 = hashlib.sha256()
+    for a, dt in ((t["pi"], "<i4"), (t["lambda_num"], "<u8"), (t["lambda_den"], "<u4")):
+        h1.update(np.ascontiguousarray(a).astype(dt).tobytes())
+    h2 = hashlib.sha256()
+    for a, dt in ((t["merges"], "<i4"), (t["h_num"], "<u8"), (t["h_den"], "<u4"),
+                  (t["sizes"], "<i4")):
+        h2.update(np.ascontiguousarray(a).astype(dt).tobytes())
+    return h1.hexdigest(), h2.hexdigest()
+
+
+def test_scale400k_prefix_trees_against_oracle_digests(fg, full):
+    gold = json.load(open(GOLDEN)) if os.path.exists(GOLDEN) else {}
+    ns = sorted(int(name[len(PREFIX):]) for name in gold if name.startswith(PREFIX))
+    if not ns:
+        pytest.skip("no oracle digest of a k=400,000 prefix stored yet")
+    res, off = full[0], full[1]
+    for n in ns:
+        want = gold[PREFIX + str(n)]
+        if n == len(off) - 1:
+            got, st = full[3], full[4]
+        else:
+            fam = fg.pack_peq(res[:off[n]], off[:n + 1])
+            got = fg.slink_tree(fam)
+            st = fam.stats()
+            fam.free()
+        assert st["update_path"] == 3
+        assert _digest(got) == (want["pi_lambda_sha256"], want["merges_sha256"]), n

@@ -119,9 +119,10 @@ def test_degenerate_families(fg):
     assert (got["lambda_den"] == 0).all()
 
 
-@pytest.mark.parametrize("path,ctas", [(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (2, 8)])
+@pytest.mark.parametrize("path,ctas", [(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (2, 8), (3, 0)])
 def test_update_paths_and_cluster_sizes_agree(fg, path, ctas):
-    # path 1: state in cluster shared memory, path 2: state in global memory
+    # insertion with the state in cluster shared memory (1) or global memory
+    # (2); minimum-spanning-tree rebuild per row block (3)
     res, off = synth.family(400, 11, root_len=150, alphabet=4, dup_frac=0.05)
     fg.debug_set_update_path(path)
     fg.debug_set_cluster(ctas)
@@ -137,11 +138,13 @@ def test_update_paths_and_cluster_sizes_agree(fg, path, ctas):
 @pytest.mark.parametrize("threads", [128, 256])
 def test_update_thread_counts_agree(fg, threads):
     res, off = synth.family(700, 41, root_len=60, alphabet=3, sub_rate=0.1)
+    fg.debug_set_update_path(1)
     fg.debug_set_update_threads(threads)
     try:
         got, st = run_tree(fg, res, off)
     finally:
         fg.debug_set_update_threads(0)
+        fg.debug_set_update_path(0)
     assert st["relayout_merges"] > 0
     assert_same_tree(got, oracle_tree(res, off))
 
@@ -207,13 +210,66 @@ def test_long_sequence_wide_keys(fg, path):
         fg.debug_set_update_path(0)
     assert st["narrow_keys"] == 0
     assert_same_tree(got, oracle_tree(res, off))
+    # the tree rebuild needs the narrow keys: forcing it on this family is an error,
+    # and the automatic choice takes an insertion kernel
+    fg.debug_set_update_path(3)
+    try:
+        fam = fg.pack_peq(res, off)
+        with pytest.raises(RuntimeError):
+            fg.slink_tree(fam)
+        fam.free()
+    finally:
+        fg.debug_set_update_path(0)
+    _, st = run_tree(fg, res, off)
+    assert st["update_path"] in (1, 2)
 
 
 def test_narrow_keys_used_for_short_families(fg):
     res, off = synth.family(300, 32, root_len=100)
     got, st = run_tree(fg, res, off)
-    assert st["update_path"] == 1 and st["narrow_keys"] == 1
+    assert st["update_path"] == 3 and st["narrow_keys"] == 1
     assert_same_tree(got, oracle_tree(res, off))
+
+
+MSF_FAMILIES = [
+    dict(k=2, seed=1, root_len=30),
+    dict(k=3, seed=3, root_len=5, alphabet=2),
+    dict(k=60, seed=4, root_len=12, alphabet=2, dup_frac=0.3),
+    dict(k=150, seed=6, root_len=20, alphabet=4, sub_rate=0.2),
+    dict(k=300, seed=8, root_len=8, alphabet=2, indel_rate=0.1, dup_frac=0.05),
+    dict(k=500, seed=21, root_len=90, alphabet=3, dup_frac=0.05),
+]
+
+
+@pytest.mark.parametrize("rows", [0, 1, 2, 7, 64])
+@pytest.mark.parametrize("fam", range(len(MSF_FAMILIES)))
+def test_tree_rebuild_over_many_row_blocks(fg, fam, rows):
+    # the minimum-spanning-tree row update rebuilds the tree once per row
+    # block; one-row blocks make it run as many times as there are points
+    res, off = synth.family(**MSF_FAMILIES[fam])
+    fg.debug_set_row_block(rows)
+    try:
+        got, st = run_tree(fg, res, off)
+    finally:
+        fg.debug_set_row_block(0)
+    assert st["update_path"] == 3
+    assert_same_tree(got, oracle_tree(res, off))
+
+
+def test_tree_rebuild_degenerate_and_infinite(fg):
+    # every distance +inf (disjoint alphabets), and all-identical sequences
+    for res, off in (
+            (np.concatenate([np.full(7, c, np.uint8) for c in range(25)]),
+             np.arange(26, dtype=np.int64) * 7),
+            (np.tile(np.arange(20, dtype=np.uint8), 40), np.arange(41, dtype=np.int64) * 20)):
+        for rows in (0, 3):
+            fg.debug_set_row_block(rows)
+            try:
+                got, st = run_tree(fg, res, off)
+            finally:
+                fg.debug_set_row_block(0)
+            assert st["update_path"] == 3
+            assert_same_tree(got, oracle_tree(res, off))
 
 
 def test_plain1k_tree(fg):
