@@ -669,8 +669,118 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res, off, args.cpu_budget)
+    if world == 1 and args.workload == "plain20k" and not args.no_extra and not args.k:
+        # the other configurations of the metric, measured in the same run:
+        # the largest single-GPU one (k=400,000) and batched against plain
+        line["config"]["batch512"] = measure_batch512(fg, args, flush)
+        line["config"]["scale400k"] = measure_scale400k(fg, args, flush)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_scale400k(fg, args, flush):
+    """The largest single-GPU configuration (k=400,000), measured after the
+    headline steps: one step through the public API with pinned host buffers
+    (the e2e figure; it also warms every kernel and allocation pool at this
+    size), then one step with the inputs resident in HBM, timed with CUDA
+    events on the launching stream and with the clocks sampled."""
+    import torch
+    res, off = make_family("scale400k", args.seed, None)
+    k = len(off) - 1
+    cells, pairs = cells_and_pairs(off)
+    pres = torch.from_numpy(res).pin_memory()
+    poff = torch.from_numpy(off).pin_memory()
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fam = fg.pack_peq(pres, poff)
+    t = fg.slink_tree(fam, device=False)
+    fam.free()
+    e2e_ms = 1e3 * (time.perf_counter() - t0)
+    d2h = sum(v.nbytes for v in t.values())
+    dres = torch.from_numpy(res).cuda()
+    doff = torch.from_numpy(off).cuda()
+    flush.zero_()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fam = fg.pack_peq(dres, doff)
+    fg.slink_tree(fam, device=True)
+    e1.record()
+    e1.synchronize()
+    st = fam.stats()
+    fam.free()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    lcs_ms = st["lcs_ns"] / 1e6
+    achieved = OPS_PER_WORD_STEP * st["word_steps"] / (lcs_ms * 1e-3) / 1e12
+    peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9 / 1e12
+    del dres, doff
+    return {"workload": WORKLOADS["scale400k"], "k": k, "cells": cells, "pairs": pairs,
+            "steps": 1, "warmup": "one e2e step of the same family first (and the headline steps "
+                                  "before it, with the same kernels)",
+            "ms_per_step": ms, "gcups": cells / (ms * 1e-3) / 1e9, "pairs_per_s": pairs / (ms * 1e-3),
+            "breakdown_ms": {"lcs_kernels": lcs_ms, "row_update_kernels": st["update_ns"] / 1e6,
+                             "finalise": st["finalize_ns"] / 1e6},
+            "gpu_launches": int(st["launches"] + st["pack_launches"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS",
+                         "frac": achieved / peak, "kernel": "k_lcs_tpp / k_lcs_wpp",
+                         "frac_all_int32_lanes": achieved / (SMS * INT32_LANES * SM_MAX_GHZ * 1e9 / 1e12)},
+            "e2e": {"value": cells / (e2e_ms * 1e-3) / 1e9, "unit": "GCUPS", "ms": e2e_ms,
+                    "h2d_bytes_per_step": int(res.nbytes + off.nbytes), "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk,
+            "l2": "256 MB buffer written before the step; inputs and working set far above L2"}
+
+
+def measure_batch512(fg, args, flush):
+    """Batched against plain on the 512-family workload: one warm-up batch step
+    (it runs the autotuner), one timed batch step (pack + plan + graph capture +
+    graph), then the same families one plain pack + tree at a time."""
+    import torch
+    import synth
+    fams = synth.batch512(args.seed)
+    res, off, fo = concat_families(fams)
+    cells = sum(cells_and_pairs(o)[0] for _, o in fams)
+    dres = torch.from_numpy(res).cuda()
+    doff = torch.from_numpy(off).cuda()
+    b = fg.batch_pack(dres, doff, fo)
+    fg.batch_tree(b, device=True)
+    b.free()
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b = fg.batch_pack(dres, doff, fo)
+    fg.batch_tree(b, device=True)
+    e1.record()
+    e1.synchronize()
+    st = b.stats()
+    b.free()
+    batch_ms = e0.elapsed_time(e1)
+    fams_dev = [(torch.from_numpy(r).cuda(), torch.from_numpy(o).cuda()) for r, o in fams]
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    for r, o in fams_dev:
+        fam = fg.pack_peq(r, o)
+        fg.slink_tree(fam, device=True)
+        fam.free()
+    e1.record()
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    lcs_ms = st["lcs_ns"] / 1e6
+    achieved = OPS_PER_WORD_STEP * st["word_steps"] / (lcs_ms * 1e-3) / 1e12
+    peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9 / 1e12
+    return {"workload": WORKLOADS["batch512"], "families": len(fams), "cells": cells,
+            "batch_ms": batch_ms, "batch_gcups": cells / (batch_ms * 1e-3) / 1e9,
+            "plain_ms": plain_ms, "plain_gcups": cells / (plain_ms * 1e-3) / 1e9,
+            "speedup_vs_plain": plain_ms / batch_ms,
+            "lcs_roofline_frac": achieved / peak,
+            "note": "batched: famsa_batch_pack + famsa_batch_tree (one CUDA graph) per step; plain: "
+                    "famsa_pack_peq + famsa_slink_tree per family, one after another on one stream; "
+                    "trees bit-exact either way (tests/test_gpu_batch.py)"}
 
 
 def run_int_peaks():
@@ -682,10 +792,10 @@ def run_int_peaks():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     out = {"sms": sms, "kinds": {}}
     for kind, name in enumerate(["lop3", "iadd3", "imad", "lop3+imad"]):
-        fg.debug_int_pipe_rate(kind)  # warm-up
+        fg.probe_int_pipe_rate(kind)  # warm-up
         clk = ClockSampler(0)
         clk.start()
-        rates = [fg.debug_int_pipe_rate(kind) for _ in range(20)]
+        rates = [fg.probe_int_pipe_rate(kind) for _ in range(20)]
         c = clk.stop()
         rate = float(np.median(rates))
         mhz = c.get("sm_mhz") or SM_MAX_GHZ * 1e3
@@ -706,8 +816,8 @@ def run_cluster_probe():
     for cl in (1, 16):
         row = {}
         for kind, name in enumerate(names):
-            fg.debug_cluster_probe(kind, cl)  # warm-up
-            row[name] = float(np.median([fg.debug_cluster_probe(kind, cl) for _ in range(5)]))
+            fg.probe_cluster(kind, cl)  # warm-up
+            row[name] = float(np.median([fg.probe_cluster(kind, cl) for _ in range(5)]))
         out["cluster_%d" % cl] = row
     print(json.dumps({"unit": "SM clocks per repetition", "threads_per_cta": 512, **out}), flush=True)
     return 0
@@ -723,6 +833,9 @@ def main():
     ap.add_argument("--k", type=int, default=None, help="override family size (testing)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="plain20k: skip the k=400,000 step and the batched-vs-plain run that "
+                         "follow the headline steps")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0,
                     help="--impl reference: host seconds of oracle work per step")

@@ -168,6 +168,21 @@ int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_of
                     void *cuda_stream);
 
 /*
+ * famsa_merge_similarity -- the merge heights as the paper's similarity
+ * LCS / indel^2 ("Pairwise similarities calculation"), a double beside the
+ * exact fractions the tree calls return.  A height num / den is the distance
+ * indel^2 / LCS, so the similarity is den / num: +infinity for height 0
+ * (identical sequences) and 0 for height +infinity (LCS 0).
+ *   h_num, h_den: n heights as returned by famsa_slink_tree or
+ *     famsa_batch_tree, ON THE DEVICE.
+ *   similarity: n doubles ON THE DEVICE (caller-owned).
+ * Stream-ordered on cuda_stream; returns after enqueue.
+ * Errors: EINVAL (NULL pointer with n > 0, n < 0), ECUDA.
+ */
+int famsa_merge_similarity(const uint64_t *h_num, const uint32_t *h_den, int64_t n,
+                           double *similarity, void *cuda_stream);
+
+/*
  * famsa_lcs_query_noalloc -- famsa_lcs_query for callers that cannot
  * allocate device memory at call time.  The paper has no counterpart: it is
  * an interface of this library only.
@@ -198,10 +213,12 @@ int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_of
  * device (cudaGetSymbolAddress), so make that first call before any stream
  * capture on the device.
  * Sharing: every call on a device uses the same array, which keeps what the
- * last call wrote there; each call rewrites all of it that it reads.  Calls
- * whose GPU work overlaps (on different streams, from different threads or
- * on different handles) race on the array: serialise them, for example on
- * one stream.
+ * last call wrote there; each call rewrites all of it that it reads.  Within
+ * one process the library holds one lock from a call's first launch until its
+ * stream has finished, so calls from several host threads (any handles, any
+ * streams) run one after another.  GPU work that overlaps a call and touches
+ * the array in another way -- a CUDA graph captured around a call and
+ * replayed beside another call -- races on it: keep such replays serialised.
  */
 #define FAMSA_NOALLOC_MAX_QUERIES 64
 #define FAMSA_NOALLOC_MAX_LEN 4096

@@ -16,6 +16,11 @@ extern "C" {
  * FAMSA_ENOMEM (n = 0: the next one); n < 0 disables.  Returns FAMSA_OK. */
 int famsa_debug_fail_alloc_after(int n);
 
+/* The number of device allocations the library has made in this process so
+ * far (every one goes through one stream-ordered allocation routine).  Tests
+ * use it to check that a call allocates nothing. */
+int64_t famsa_debug_alloc_count(void);
+
 /* Rows wider than w 64-bit words use the warp-per-pair LCS kernel instead of
  * thread-per-pair (default 32, the thread-per-pair maximum; 0 sends every
  * row to warp-per-pair).  Results are identical either way.  Returns
@@ -82,21 +87,6 @@ int famsa_debug_set_autotune(int on);
  * row block's size (512 below 100,000 points, else 1,024), 0 1,024, 1 512.
  * Results are identical.  EINVAL outside -1..1. */
 int famsa_debug_set_global_variant(int v);
-
-/* Thread-instructions per second of one integer instruction kind run as
- * many independent chains over the whole device (kind 0 LOP3, 1 IADD3,
- * 2 IMAD, 3 LOP3 and IMAD alternating); it measures the width of the ALU
- * and FMA pipes for the LCS roofline.  Allocates a small output buffer. */
-int famsa_debug_int_pipe_rate(int kind, double *inst_per_s);
-
-/* SM clocks per repetition of one building block of the row update, on one
- * cluster of cluster_ctas (1, 2, 4, 8 or 16) CTAs of 512 threads, timed by
- * thread 0 of CTA 0 over 4,096 repetitions: kind 0 the block clamp scan with
- * order-code keys, 1 the same with cross-multiplied keys, 2 a cluster
- * barrier, 3 every CTA pushing one clamp into every CTA's shared memory and
- * a cluster barrier, 4 a dependent load from local shared memory, 5 a
- * dependent load from the next CTA's shared memory.  Allocates a few KB. */
-int famsa_debug_cluster_probe(int kind, int cluster_ctas, double *cycles);
 
 /* on != 0 (default): families of up to 4,096 points are finalised by one
  * CTA in one launch; 0: every family takes the multi-kernel finalisation.

@@ -97,11 +97,11 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_cluster": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_alloc_count": ([], ctypes.c_int64),
+            "famsa_merge_similarity": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
             "famsa_debug_set_serial": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
-            "famsa_debug_int_pipe_rate": ([ctypes.c_int, _P], ctypes.c_int),
-            "famsa_debug_cluster_probe": ([ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
             "famsa_debug_set_global_variant": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_fin_small": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_order_code": ([ctypes.c_uint32, ctypes.c_uint32, _P], ctypes.c_int),
@@ -147,6 +147,26 @@ def _ptr(x):
     if not x.flags["C_CONTIGUOUS"]:
         raise ValueError("array must be C-contiguous")
     return x.ctypes.data, False
+
+
+_TORCH_DT = {"uint8": "uint8", "int32": "int32", "int64": "int64", "uint32": "uint32",
+             "uint64": "uint64"}
+
+
+def _require(x, dtype, name, count=None, at_least=None):
+    """Refuse a buffer of the wrong element type or size before the library sees
+    its pointer (the library trusts the sizes it is given)."""
+    want = np.dtype(dtype).name
+    if _is_torch(x):
+        got, n = str(x.dtype).replace("torch.", ""), x.numel()
+    else:
+        got, n = np.asarray(x).dtype.name, np.asarray(x).size
+    if got != _TORCH_DT[want]:
+        raise ValueError("%s must be %s, not %s" % (name, want, got))
+    if count is not None and n != count:
+        raise ValueError("%s must have %d elements, not %d" % (name, count, n))
+    if at_least is not None and n < at_least:
+        raise ValueError("%s needs at least %d elements, has %d" % (name, at_least, n))
 
 
 def _stream_ptr(stream):
@@ -205,6 +225,8 @@ class Family:
 def famsa_pack_peq(residues, offsets, stream=None) -> Family:
     """Validate a family, copy it to the device and build its Peq tables."""
     lib = load()
+    _require(residues, np.uint8, "residues")
+    _require(offsets, np.int64, "offsets")
     rp, rdev = _ptr(residues)
     op, odev = _ptr(offsets)
     if rdev != odev:
@@ -224,6 +246,7 @@ def famsa_lcs_allpairs(fam: Family, out=None, device: bool = False, stream=None)
     n = fam.k * (fam.k - 1) // 2
     if out is None:
         out = _empty(n, np.int32, device)
+    _require(out, np.int32, "out", at_least=n)
     p, dev = _ptr(out)
     _check(load().famsa_lcs_allpairs(fam.handle, p, int(dev), _stream_ptr(stream)),
            "famsa_lcs_allpairs")
@@ -239,6 +262,7 @@ def famsa_lcs_rows(fam: Family, row_begin: int, row_end: int, out=None, device: 
     n = (row_end * (row_end - 1) - row_begin * (row_begin - 1)) // 2
     if out is None:
         out = _empty(max(n, 0), np.int32, device)
+    _require(out, np.int32, "out", at_least=max(n, 0))
     p, dev = _ptr(out)
     _check(load().famsa_lcs_rows(fam.handle, row_begin, row_end, p, int(dev), _stream_ptr(stream)),
            "famsa_lcs_rows")
@@ -263,13 +287,27 @@ def famsa_encode_ascii(text) -> np.ndarray:
 encode_ascii = famsa_encode_ascii
 
 
-def merge_similarity(tree: dict) -> np.ndarray:
+def famsa_merge_similarity(tree: dict, stream=None):
     """The merge heights as the paper's similarity LCS / indel^2 (= h_den / h_num),
-    a float64 convenience beside the exact fractions; +inf for height 0."""
-    num = np.asarray(tree["h_num"], dtype=np.float64)
-    den = np.asarray(tree["h_den"], dtype=np.float64)
-    with np.errstate(divide="ignore"):
-        return np.where(num == 0, np.inf, den / np.where(num == 0, 1, num))
+    computed by the library on the device: +inf for height 0, 0 for +inf.
+    Device tensors in give a device tensor out; host arrays are copied over and back."""
+    import torch
+    num, den = tree["h_num"], tree["h_den"]
+    on_host = not _is_torch(num)
+    if on_host:
+        num = torch.from_numpy(np.ascontiguousarray(num, dtype=np.uint64)).cuda()
+        den = torch.from_numpy(np.ascontiguousarray(den, dtype=np.uint32)).cuda()
+    _require(num, np.uint64, "h_num")
+    _require(den, np.uint32, "h_den", count=num.numel())
+    out = torch.empty(num.numel(), dtype=torch.float64, device=num.device)
+    _check(load().famsa_merge_similarity(num.data_ptr(), den.data_ptr(), num.numel(), out.data_ptr(),
+                                         _stream_ptr(stream)), "famsa_merge_similarity")
+    if on_host:
+        return out.cpu().numpy()
+    return out
+
+
+merge_similarity = famsa_merge_similarity
 
 
 def famsa_slink_tree(fam: Family, device: bool = False, stream=None) -> dict:
@@ -327,6 +365,8 @@ class Batch:
 
 def famsa_batch_pack(residues, offsets, family_offsets, stream=None) -> Batch:
     """Pack many families (one sequence list split by host family_offsets)."""
+    _require(residues, np.uint8, "residues")
+    _require(offsets, np.int64, "offsets")
     rp, rdev = _ptr(residues)
     op, odev = _ptr(offsets)
     if rdev != odev:
@@ -461,6 +501,10 @@ def famsa_lcs_query(fam: Family, q_residues, q_offsets, out=None, device: bool =
                     stream=None):
     """LCS of each query against every member: (nq, k) int32."""
     nq = len(q_offsets) - 1
+    _require(q_residues, np.uint8, "q_residues")
+    _require(q_offsets, np.int64, "q_offsets", count=nq + 1)
+    if out is not None:
+        _require(out, np.int32, "out", at_least=nq * fam.k)
     qp, qdev = _ptr(q_residues)
     op, odev = _ptr(q_offsets)
     if qdev != odev:
@@ -482,6 +526,10 @@ def famsa_lcs_query_noalloc(fam: Family, q_residues, q_offsets, max_len: int, ou
     and output only, at most NOALLOC_MAX_QUERIES queries of at most
     NOALLOC_MAX_LEN residues (max_len bounds them all); (nq, k) int32."""
     nq = len(q_offsets) - 1
+    _require(q_residues, np.uint8, "q_residues")
+    _require(q_offsets, np.int64, "q_offsets", count=nq + 1)
+    if out is not None:
+        _require(out, np.int32, "out", at_least=nq * fam.k)
     qp, qdev = _ptr(q_residues)
     op, odev = _ptr(q_offsets)
     if not (qdev and odev):
@@ -529,6 +577,11 @@ def debug_insertion_state(fam: Family) -> dict:
     return out
 
 
+def debug_alloc_count() -> int:
+    """Device allocations made by the library in this process so far."""
+    return int(load().famsa_debug_alloc_count())
+
+
 def debug_set_row_block(rows: int):
     """Rows per row block of the tree build (0 = automatic)."""
     _check(load().famsa_debug_set_row_block(rows), "famsa_debug_set_row_block")
@@ -549,19 +602,40 @@ def debug_sub_kcycles(fam: Family):
     return out.tolist()
 
 
-def debug_int_pipe_rate(kind: int) -> float:
+_probe_lib = None
+PROBE_LIB_PATH = os.path.join(_HERE, "libfamsa_probe.so")
+PROBE_HEADER = os.path.join(INCLUDE, "famsa_probe.h")
+
+
+def load_probes(path: str = PROBE_LIB_PATH):
+    """The benchmark's microbenchmark library (libfamsa_probe.so), separate from the product."""
+    global _probe_lib
+    with _lock:
+        if _probe_lib is None:
+            if not os.path.exists(path):
+                raise ImportError("libfamsa_probe.so not built: run python -m paper_1603_06958_gb300.build")
+            lib = ctypes.CDLL(path)
+            lib.famsa_probe_int_pipe_rate.argtypes = [ctypes.c_int, _P]
+            lib.famsa_probe_int_pipe_rate.restype = ctypes.c_int
+            lib.famsa_probe_cluster.argtypes = [ctypes.c_int, ctypes.c_int, _P]
+            lib.famsa_probe_cluster.restype = ctypes.c_int
+            _probe_lib = lib
+    return _probe_lib
+
+
+def probe_int_pipe_rate(kind: int) -> float:
     """Thread-instructions/s of independent LOP3 (0), IADD3 (1), IMAD (2) or
     LOP3+IMAD (3) chains over the whole device."""
     out = ctypes.c_double()
-    _check(load().famsa_debug_int_pipe_rate(kind, ctypes.byref(out)), "famsa_debug_int_pipe_rate")
+    _check(load_probes().famsa_probe_int_pipe_rate(kind, ctypes.byref(out)), "famsa_probe_int_pipe_rate")
     return out.value
 
 
-def debug_cluster_probe(kind: int, cluster_ctas: int = 16) -> float:
-    """SM clocks per repetition of a row-update building block (see the C header)."""
+def probe_cluster(kind: int, cluster_ctas: int = 16) -> float:
+    """SM clocks per repetition of a row-update building block (see famsa_probe.h)."""
     out = ctypes.c_double()
-    _check(load().famsa_debug_cluster_probe(int(kind), int(cluster_ctas), ctypes.byref(out)),
-           "famsa_debug_cluster_probe")
+    _check(load_probes().famsa_probe_cluster(int(kind), int(cluster_ctas), ctypes.byref(out)),
+           "famsa_probe_cluster")
     return out.value
 
 

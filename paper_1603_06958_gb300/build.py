@@ -17,8 +17,12 @@ ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu", "lcs_tpp_d.cu",
            "lcs_wpp.cu", "slink.cu", "slink_global.cu", "slink_smem.cu", "slink_msf.cu", "finalize.cu",
-           "noalloc.cu", "int_peak.cu", "batch.cu", "server.cu", "cluster_probe.cu"]
-HEADERS = ["famsa_internal.cuh", "lcs_kernels.cuh", "lcs_step.inc", "slink_common.cuh", "slink_msf.cuh",
+           "noalloc.cu", "batch.cu", "server.cu"]
+# microbenchmarks behind the roofline figures: a separate library that only
+# bench.py loads (--int-peaks, --cluster-probe), not part of the product ABI
+PROBE_SOURCES = ["probes/int_peak.cu", "probes/cluster_probe.cu"]
+PROBE_LIB = os.path.join(HERE, "libfamsa_probe.so")
+HEADERS = [os.path.join(ROOT, "include", "famsa_probe.h"), "famsa_internal.cuh", "lcs_kernels.cuh", "lcs_step.inc", "slink_common.cuh", "slink_msf.cuh",
            "slink_merge.cuh", os.path.join(ROOT, "include", "famsa_gpu_debug.h"),
            os.path.join(ROOT, "include", "famsa_gpu.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -47,15 +51,14 @@ def _gen_step():
         os.replace(inc + ".tmp", inc)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
+def _build_lib(sources, lib, force, verbose, ptxas_v):
     os.makedirs(OBJ, exist_ok=True)
-    _gen_step()
     hdr = max(_mtime(h if os.path.isabs(h) else os.path.join(CSRC, h)) for h in HEADERS)
     jobs = []
     objs = []
-    for s in SOURCES:
+    for s in sources:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OBJ, s.replace(".cu", ".o"))
+        obj = os.path.join(OBJ, s.replace("/", "_").replace(".cu", ".o"))
         objs.append(obj)
         if force or _mtime(obj) < max(_mtime(src), hdr):
             cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_v else []) + \
@@ -71,13 +74,20 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
                 if r.returncode != 0:
                     sys.stderr.write(" ".join(j) + "\n" + r.stdout + r.stderr)
                     raise RuntimeError("nvcc failed for %s" % j[-3])
-    if force or jobs or _mtime(LIB) < max(_mtime(o) for o in objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _mtime(lib) < max(_mtime(o) for o in objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
+    """Build libfamsa_gpu.so (and the benchmark's probe library beside it)."""
+    _gen_step()
+    _build_lib(SOURCES, LIB, force, verbose, ptxas_v)
+    _build_lib(PROBE_SOURCES, PROBE_LIB, force, verbose, ptxas_v)
     return LIB
 
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv)
-    print(LIB)

@@ -27,7 +27,7 @@ static void host_row_list(const Family *f, RowList &rl) {
 
 template <typename T>
 static cudaError_t upload(const std::vector<T> &v, T **d, cudaStream_t st) {
-  cudaError_t e = cudaMallocAsync((void **)d, std::max<size_t>(v.size(), 1) * sizeof(T), st);
+  cudaError_t e = lib_malloc_async((void **)d, std::max<size_t>(v.size(), 1) * sizeof(T), st);
   if (e != cudaSuccess) { *d = nullptr; return e; }
   if (!v.empty()) e = cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
   return e;
@@ -141,7 +141,7 @@ int famsa_lcs_allpairs(const famsa_family *fh, int32_t *lcs_out, int out_on_devi
   RowList rl;
   host_row_list(f, rl);
   if (!out_on_device) {
-    err = cudaMallocAsync((void **)&d_out, sizeof(int32_t) * n, st);
+    err = lib_malloc_async((void **)&d_out, sizeof(int32_t) * n, st);
     if (err != cudaSuccess) return status_from_cuda(err);
   }
   err = upload(rl.id, &rl.d_id, st);
@@ -206,7 +206,7 @@ int famsa_lcs_rows(const famsa_family *fh, int32_t row_begin, int32_t row_end, i
     for (size_t e = 0; e < m; ++e) h_po[e] = all[ids[e]];
   }
   if (err == cudaSuccess && !out_on_device)
-    err = cudaMallocAsync((void **)&d_out, sizeof(int32_t) * n, st);
+    err = lib_malloc_async((void **)&d_out, sizeof(int32_t) * n, st);
   if (err == cudaSuccess) err = upload(ids, &d_ids, st);
   if (err == cudaSuccess) err = upload(orig, &d_orig, st);
   if (err == cudaSuccess) err = upload(len, &d_len, st);
@@ -255,8 +255,8 @@ int famsa_lcs_query(const famsa_family *fh, const uint8_t *q, const int64_t *q_o
     for (int32_t i = 0; i < nq; ++i)
       if (q_offsets[i + 1] <= q_offsets[i]) return FAMSA_EINVAL;
     int64_t total = q_offsets[nq];
-    err = cudaMallocAsync((void **)&own_q, std::max<int64_t>(total, 1), st);
-    if (err == cudaSuccess) err = cudaMallocAsync((void **)&own_off, sizeof(int64_t) * (nq + 1), st);
+    err = lib_malloc_async((void **)&own_q, std::max<int64_t>(total, 1), st);
+    if (err == cudaSuccess) err = lib_malloc_async((void **)&own_off, sizeof(int64_t) * (nq + 1), st);
     if (err == cudaSuccess) err = cudaMemcpyAsync(own_q, q, total, cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(own_off, q_offsets, sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st);
@@ -296,7 +296,7 @@ int famsa_lcs_query(const famsa_family *fh, const uint8_t *q, const int64_t *q_o
   const int64_t n = (int64_t)nq * f->k;
   int32_t *d_out = out, *d_ids = nullptr, *d_len = nullptr;
   int64_t *d_po = nullptr;
-  if (!out_on_device) err = cudaMallocAsync((void **)&d_out, sizeof(int32_t) * n, st);
+  if (!out_on_device) err = lib_malloc_async((void **)&d_out, sizeof(int32_t) * n, st);
   if (err == cudaSuccess) err = upload(order, &d_ids, st);
   if (err == cudaSuccess) err = upload(len, &d_len, st);
   if (err == cudaSuccess) err = upload(po, &d_po, st);

@@ -84,6 +84,10 @@ struct Family {
   std::vector<int64_t> dbg_state;
 };
 
+// Every device allocation of the library goes through lib_malloc_async
+// (stream-ordered cudaMallocAsync), which counts them process-wide for
+// famsa_debug_alloc_count.
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t st);
 // Allocation with an injectable failure hook (tests use it to check ENOMEM paths).
 // Stream-ordered (cudaMallocAsync / cudaFreeAsync) on the calling thread's
 // allocation stream, so that freeing never waits for the whole device.

@@ -439,3 +439,24 @@ extern "C" int famsa_debug_set_fin_small(int on) {
   famsa::g_fin_small = on ? famsa::kFinSmall : 0;
   return FAMSA_OK;
 }
+
+namespace famsa {
+// similarity = LCS / indel^2 = den / num of a height num / den (distance indel^2 / LCS)
+__global__ void k_merge_similarity(const uint64_t *num, const uint32_t *den, int64_t n, double *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t a = num[i];
+  const uint32_t b = den[i];
+  out[i] = b == 0 ? 0.0 : (a == 0 ? __longlong_as_double(0x7ff0000000000000LL) : (double)b / (double)a);
+}
+}  // namespace famsa
+
+extern "C" int famsa_merge_similarity(const uint64_t *h_num, const uint32_t *h_den, int64_t n,
+                                      double *similarity, void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!h_num || !h_den || !similarity))) return FAMSA_EINVAL;
+  if (n == 0) return FAMSA_OK;
+  const int T = 256;
+  famsa::k_merge_similarity<<<(unsigned)((n + T - 1) / T), T, 0, (cudaStream_t)cuda_stream>>>(
+      h_num, h_den, n, similarity);
+  return famsa::status_from_cuda(cudaGetLastError());
+}

@@ -104,7 +104,8 @@ __global__ void k_noalloc_peq(const uint8_t *q, const int64_t *q_off, int32_t nq
 }
 
 constexpr int kNoAllocMaxDevices = 64;
-static std::mutex g_noalloc_mu;
+static std::mutex g_noalloc_mu;       // the per-device address table
+static std::mutex g_noalloc_call_mu;  // one call at a time owns the array
 static void *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
 // Device address of the array on the current device, looked up once per
@@ -140,6 +141,10 @@ extern "C" int famsa_lcs_query_noalloc(const famsa_family *fh, const uint8_t *q,
   if (rc != FAMSA_OK) return rc;
   const NoAllocView v = view_of(base);
   const int32_t W = (max_len + 63) / 64;
+  // held from the first launch until the stream has finished (the call waits
+  // for it anyway), so calls from other threads cannot interleave their
+  // kernels with this call's use of the shared array
+  std::lock_guard<std::mutex> call_lk(g_noalloc_call_mu);
   std::lock_guard<std::mutex> lk(f->mu);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   k_noalloc_rows<<<1, kNoAllocMaxQueries, 0, st>>>(q_offsets, nq, max_len, W, v);

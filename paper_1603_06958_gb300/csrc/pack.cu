@@ -20,6 +20,13 @@ static thread_local cudaStream_t tl_alloc_stream = nullptr;
 AllocStream::AllocStream(cudaStream_t st) : prev(tl_alloc_stream) { tl_alloc_stream = st; }
 AllocStream::~AllocStream() { tl_alloc_stream = prev; }
 
+// every device allocation of the library, counted process-wide
+static std::atomic<int64_t> g_alloc_count{0};
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+  g_alloc_count.fetch_add(1);
+  return cudaMallocAsync(p, bytes, st);
+}
+
 cudaError_t dev_alloc(void **p, size_t bytes) {
   int n = g_alloc_fail_after.load();
   if (n >= 0) {
@@ -27,7 +34,7 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
     g_alloc_fail_after.store(n - 1);
   }
   if (bytes == 0) bytes = 16;
-  return cudaMallocAsync(p, bytes, tl_alloc_stream);
+  return lib_malloc_async(p, bytes, tl_alloc_stream);
 }
 void dev_free(void *p) {
   if (p) cudaFreeAsync(p, tl_alloc_stream);
@@ -376,9 +383,9 @@ int pack_rows(const uint8_t *d_res, const int64_t *d_off, int32_t n, cudaStream_
   std::vector<int64_t> h_off(n + 1);
   int h_status[2] = {0, 0};
   const int T = 256;
-  CK(cudaMallocAsync((void **)&d_status, sizeof(int) * 2, st));
-  CK(cudaMallocAsync((void **)d_len, sizeof(int32_t) * n, st));
-  CK(cudaMallocAsync((void **)&rebased, sizeof(int64_t) * (n + 1), st));
+  CK(lib_malloc_async((void **)&d_status, sizeof(int) * 2, st));
+  CK(lib_malloc_async((void **)d_len, sizeof(int32_t) * n, st));
+  CK(lib_malloc_async((void **)&rebased, sizeof(int64_t) * (n + 1), st));
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 2, st));
   k_lengths<<<blocks_for(n + 1, T), T, 0, st>>>(d_off, n, 0, *d_len, rebased, d_status,
                                                 d_status + 1);
@@ -403,8 +410,8 @@ int pack_rows(const uint8_t *d_res, const int64_t *d_off, int32_t n, cudaStream_
       h_len[i] = (int32_t)(h_off[i + 1] - h_off[i]);
       h_po[i + 1] = h_po[i] + (h_len[i] + 63) / 64;
     }
-    CK(cudaMallocAsync((void **)d_peq_off, sizeof(int64_t) * (n + 1), st));
-    CK(cudaMallocAsync((void **)d_peq, sizeof(uint32_t) * kPeqWordU32 * (size_t)std::max<int64_t>(h_po[n], 1), st));
+    CK(lib_malloc_async((void **)d_peq_off, sizeof(int64_t) * (n + 1), st));
+    CK(lib_malloc_async((void **)d_peq, sizeof(uint32_t) * kPeqWordU32 * (size_t)std::max<int64_t>(h_po[n], 1), st));
     CK(cudaMemcpyAsync(*d_peq_off, h_po.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
     k_pack_peq<<<blocks_for((int64_t)n * 32, T), T, 0, st>>>(d_res, d_off, nullptr, *d_peq_off, n,
                                                             *d_peq);
@@ -430,3 +437,5 @@ extern "C" int famsa_debug_fail_alloc_after(int n) {
   famsa::g_alloc_fail_after.store(n);
   return 0;
 }
+
+extern "C" int64_t famsa_debug_alloc_count(void) { return famsa::g_alloc_count.load(); }

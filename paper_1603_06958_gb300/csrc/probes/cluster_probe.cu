@@ -5,8 +5,8 @@
 // from local shared memory and from another CTA's shared memory (DSMEM).
 // These are the figures behind the choice of the order-code keys and of
 // pushing the cross-CTA values before a barrier.
-#include "famsa_gpu_debug.h"
-#include "slink_common.cuh"
+#include "famsa_probe.h"
+#include "../slink_common.cuh"
 
 namespace famsa {
 
@@ -84,7 +84,7 @@ static cudaError_t run_probe(int cl, int iters, unsigned long long *out, uint64_
 
 }  // namespace famsa
 
-extern "C" int famsa_debug_cluster_probe(int kind, int cluster_ctas, double *cycles) {
+extern "C" int famsa_probe_cluster(int kind, int cluster_ctas, double *cycles) {
   using namespace famsa;
   if (kind < 0 || kind > 5 || !cycles) return FAMSA_EINVAL;
   if (cluster_ctas != 1 && cluster_ctas != 2 && cluster_ctas != 4 && cluster_ctas != 8 && cluster_ctas != 16)
@@ -109,7 +109,7 @@ extern "C" int famsa_debug_cluster_probe(int kind, int cluster_ctas, double *cyc
   if (err == cudaSuccess) err = cudaMemcpy(&h, out, sizeof(h), cudaMemcpyDeviceToHost);
   cudaFree(out);
   cudaFree(sink);
-  if (err != cudaSuccess) return status_from_cuda(err);
+  if (err != cudaSuccess) return (err == cudaErrorMemoryAllocation ? FAMSA_ENOMEM : FAMSA_ECUDA);
   *cycles = (double)h / iters;
   return FAMSA_OK;
 }

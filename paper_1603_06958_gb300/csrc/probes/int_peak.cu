@@ -4,8 +4,8 @@
 // issue on the ALU pipe only; IMAD issues on the FMA (heavy) pipe.  These
 // kernels run many independent chains of one instruction kind (or an even
 // LOP3/IMAD mix) so the measured instruction rate shows each pipe's width.
-#include "famsa_internal.cuh"
-#include "famsa_gpu_debug.h"
+#include "../famsa_internal.cuh"
+#include "famsa_probe.h"
 
 namespace famsa {
 
@@ -36,17 +36,17 @@ __global__ void __launch_bounds__(256) k_int_peak(uint32_t seed, int iters, uint
 
 }  // namespace famsa
 
-extern "C" int famsa_debug_int_pipe_rate(int kind, double *inst_per_s) {
+extern "C" int famsa_probe_int_pipe_rate(int kind, double *inst_per_s) {
   using namespace famsa;
   if (kind < 0 || kind > 3 || !inst_per_s) return FAMSA_EINVAL;
   int dev = 0, sms = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (err != cudaSuccess) return status_from_cuda(err);
+  if (err != cudaSuccess) return (err == cudaErrorMemoryAllocation ? FAMSA_ENOMEM : FAMSA_ECUDA);
   const int blocks = sms * 8, threads = 256, iters = 8192;
   uint32_t *out = nullptr;
   err = cudaMalloc((void **)&out, sizeof(uint32_t) * blocks * threads);
-  if (err != cudaSuccess) return status_from_cuda(err);
+  if (err != cudaSuccess) return (err == cudaErrorMemoryAllocation ? FAMSA_ENOMEM : FAMSA_ECUDA);
   cudaEvent_t a = nullptr, b = nullptr;
   float ms = 0.f;
   err = cudaEventCreate(&a);
@@ -67,7 +67,7 @@ extern "C" int famsa_debug_int_pipe_rate(int kind, double *inst_per_s) {
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   cudaFree(out);
-  if (err != cudaSuccess) return status_from_cuda(err);
+  if (err != cudaSuccess) return (err == cudaErrorMemoryAllocation ? FAMSA_ENOMEM : FAMSA_ECUDA);
   *inst_per_s = (double)blocks * threads * iters * kPeakChains / (ms * 1e-3);
   return FAMSA_OK;
 }

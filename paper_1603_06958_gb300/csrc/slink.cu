@@ -35,7 +35,7 @@ struct Scratch {
   T *get(size_t n) {
     void *p = nullptr;
     if (err != cudaSuccess) return nullptr;
-    err = cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), st);
+    err = lib_malloc_async(&p, std::max<size_t>(n, 1) * sizeof(T), st);
     if (err != cudaSuccess) return nullptr;
     ptrs.push_back(p);
     return static_cast<T *>(p);

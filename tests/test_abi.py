@@ -4,6 +4,7 @@ No compute calls here: there is no GPU in this environment.  Argument checks
 that fail before any device work are exercised too.
 """
 import ctypes
+import re
 import subprocess
 
 import numpy as np
@@ -28,6 +29,19 @@ def test_exports_every_declared_symbol(lib):
     for name in declared:
         assert name in exported, name
         assert getattr(lib, name) is not None
+
+
+def test_probes_live_in_their_own_library(lib):
+    # the roofline microbenchmarks are not part of the product ABI
+    out = subprocess.check_output(["nm", "-D", "--defined-only", fg.LIB_PATH], text=True)
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    assert not any("probe" in name for name in exported)
+    text = open(fg.PROBE_HEADER).read()
+    names = set(re.findall(r"^int\s+(famsa_probe_[a-z0-9_]+)\s*\(", text, re.M))
+    assert names == {"famsa_probe_int_pipe_rate", "famsa_probe_cluster"}
+    out = subprocess.check_output(["nm", "-D", "--defined-only", fg.PROBE_LIB_PATH], text=True)
+    pexported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    assert names <= pexported
 
 
 def test_strerror_and_version(lib):
@@ -74,3 +88,28 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
             mod.load(str(tmp_path / "missing.so"))
         finally:
             mod._lib = saved
+
+
+def test_binding_refuses_wrong_types_and_sizes(lib):
+    # the library trusts the sizes it is given, so the binding checks types
+    # and lengths before a pointer crosses the boundary
+    res = np.zeros(4, np.uint8)
+    with pytest.raises(ValueError):
+        fg.pack_peq(res.astype(np.int32), np.array([0, 2, 4], np.int64))
+    with pytest.raises(ValueError):
+        fg.pack_peq(res, np.array([0, 2, 4], np.int32))
+    fam = fg.Family.__new__(fg.Family)
+    fam.handle, fam.k = None, 10
+    q, qo = np.zeros(6, np.uint8), np.array([0, 3, 6], np.int64)
+    with pytest.raises(ValueError):
+        fg.lcs_query(fam, q, qo.astype(np.int32))
+    with pytest.raises(ValueError):
+        fg.lcs_query(fam, q, qo, out=np.zeros(19, np.int32))
+    with pytest.raises(ValueError):
+        fg.lcs_query(fam, q, qo, out=np.zeros(20, np.int64))
+    with pytest.raises(ValueError):
+        fg.lcs_query_noalloc(fam, q, qo.astype(np.int32), 3)
+    with pytest.raises(ValueError):
+        fg.lcs_allpairs(fam, out=np.zeros(44, np.int32))
+    with pytest.raises(ValueError):
+        fg.lcs_rows(fam, 2, 4, out=np.zeros(4, np.int32))

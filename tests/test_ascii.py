@@ -42,9 +42,3 @@ def test_encode_null_and_negative_length(lib):
     assert lib.famsa_encode_ascii(None, 4, out.ctypes.data, None) == fg.FAMSA_EINVAL
     assert lib.famsa_encode_ascii(b"ACDE", -1, out.ctypes.data, None) == fg.FAMSA_EINVAL
     assert lib.famsa_encode_ascii(b"ACDE", 4, None, None) == fg.FAMSA_EINVAL
-
-
-def test_merge_similarity_view():
-    tree = {"h_num": np.array([0, 4, 9, 1], np.uint64), "h_den": np.array([1, 2, 3, 0], np.uint32)}
-    sim = fg.merge_similarity(tree)
-    assert sim[0] == np.inf and sim[1] == 0.5 and abs(sim[2] - 1 / 3) < 1e-15 and sim[3] == 0.0

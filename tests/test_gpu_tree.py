@@ -315,3 +315,18 @@ def test_plain20k_full_tree_against_oracle_digest(fg):
     k = len(off) - 1
     pi = got["pi"]
     assert (pi[:-1] > np.arange(k - 1)).all() and pi[-1] == k - 1
+
+
+def test_merge_similarity_on_the_device(fg):
+    # the paper's similarity LCS / indel^2 of each merge height num / den is
+    # den / num; both are exact doubles, so the device division equals the
+    # correctly rounded quotient
+    tree = {"h_num": np.array([0, 4, 9, 1, 7], np.uint64), "h_den": np.array([1, 2, 3, 0, 7], np.uint32)}
+    sim = fg.merge_similarity(tree)
+    assert sim[0] == np.inf and sim[1] == 0.5 and sim[2] == 1 / 3 and sim[3] == 0.0 and sim[4] == 1.0
+    res, off = synth.family(300, 5, root_len=120)
+    got, _ = run_tree(fg, res, off)
+    sim = fg.merge_similarity(got)
+    want = [np.inf if n == 0 else (0.0 if d == 0 else int(d) / int(n))
+            for n, d in zip(got["h_num"], got["h_den"])]
+    assert np.array_equal(sim, np.array(want))

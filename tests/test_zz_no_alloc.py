@@ -3,7 +3,10 @@
 The no-allocation variant keeps its scratch in one fixed device array that
 every call shares; two calls in a row with different query sets (the second
 smaller and narrower, so the first call's leftovers sit around it) must both
-give exactly the values of the allocating entry point.
+give exactly the values of the allocating entry point.  The library's
+allocation count shows that warmed-up calls allocate nothing, and calls from
+several host threads on their own streams still give each thread its own
+values.
 """
 import ctypes
 
@@ -62,6 +65,77 @@ def test_noalloc_matches_lcs_query_on_two_calls_in_a_row(fg):
             rc, got2 = _noalloc(fg, fam, qd, od, min(4 * max_len, fg.NOALLOC_MAX_LEN))
             assert rc == fg.FAMSA_OK
             assert torch.equal(got2, want)
+    finally:
+        fam.free()
+
+
+def test_noalloc_makes_no_device_allocation(fg):
+    # every device allocation of the library goes through one counted routine:
+    # the allocating query call moves the count, warmed-up no-alloc calls do not
+    import torch
+    res, off = synth.family(120, 76, root_len=200)
+    fam = fg.pack_peq(_dev(res), _dev(off))
+    try:
+        q, o = synth.family(9, 77, root_len=180)
+        qd, od = _dev(q), _dev(o)
+        max_len = int(np.diff(o).max())
+        rc, _ = _noalloc(fg, fam, qd, od, max_len)  # the first call on the device sets up
+        assert rc == fg.FAMSA_OK
+        c0 = fg.debug_alloc_count()
+        want = fg.lcs_query(fam, q, o)  # host inputs and output: allocates
+        assert fg.debug_alloc_count() > c0
+        c1 = fg.debug_alloc_count()
+        for _ in range(2):
+            rc, got = _noalloc(fg, fam, qd, od, max_len)
+            assert rc == fg.FAMSA_OK
+            torch.cuda.synchronize()
+            assert np.array_equal(got.cpu().numpy(), want)
+        assert fg.debug_alloc_count() == c1
+    finally:
+        fam.free()
+
+
+def test_noalloc_from_several_threads(fg):
+    # calls from several host threads on their own streams run one at a time
+    # on the shared array, each with its own queries
+    import threading
+    import torch
+    res, off = synth.family(200, 78, root_len=300)
+    fam = fg.pack_peq(_dev(res), _dev(off))
+    try:
+        sets = [synth.family(5 + 3 * t, 80 + t, root_len=100 + 90 * t) for t in range(4)]
+        wants = [fg.lcs_query(fam, q, o) for q, o in sets]
+        got = [None] * len(sets)
+        errors = []
+
+        def worker(t):
+            try:
+                q, o = sets[t]
+                stream = torch.cuda.Stream()
+                with torch.cuda.stream(stream):
+                    qd, od = _dev(q), _dev(o)
+                    for _ in range(3):
+                        nq = len(o) - 1
+                        out = torch.full((nq * fam.k,), -1, dtype=torch.int32, device="cuda")
+                        rc = fg.load().famsa_lcs_query_noalloc(
+                            ctypes.c_void_p(fam.handle), ctypes.c_void_p(qd.data_ptr()),
+                            ctypes.c_void_p(od.data_ptr()), nq, int(np.diff(o).max()),
+                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+                        if rc != fg.FAMSA_OK:
+                            errors.append(rc)
+                    stream.synchronize()
+                    got[t] = out.reshape(nq, fam.k).cpu().numpy()
+            except Exception as e:  # reported below
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(t,)) for t in range(len(sets))]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errors, errors
+        for g, w in zip(got, wants):
+            assert np.array_equal(g, w)
     finally:
         fam.free()
 
