@@ -168,6 +168,52 @@ int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_of
                     void *cuda_stream);
 
 /*
+ * Sharding the pair set across devices ("Pairwise similarities calculation":
+ * the pairs are independent; "Determination of the guide tree": single
+ * linkage).  Single linkage depends only on a minimum spanning tree of the
+ * distance graph, and the minimum spanning tree of a union of edge sets is
+ * the minimum spanning tree of the union of their minimum spanning forests.
+ * So each device takes a range of rows, reduces the pairs of those rows to a
+ * forest with famsa_msf_rows, the forests are exchanged (fewer than k edges
+ * each), and famsa_tree_from_edges builds exactly the tree famsa_slink_tree
+ * gives for the whole family.
+ *
+ * famsa_msf_rows -- the minimum spanning tree of the pairs (i, j) with i in
+ * the rows [row_begin, row_end) and j < i, where rows are the points in the
+ * family's internal order (1 <= row_begin < row_end <= k; rows [1, k) cover
+ * every pair once, so any partition of them into ranges shards the pairs).
+ * Those pairs join points 0..row_end-1, so the tree has row_end - 1 edges.
+ *   edge_a[e] < edge_b[e]: the edge's two points in the caller's labels;
+ *   h_num[e] / h_den[e]: its distance indel^2 / LCS in lowest terms
+ *     (+inf = 1 / 0).  row_end - 1 entries each; on the device iff
+ *     out_on_device != 0 (otherwise the call waits for its stream).
+ * Errors: EINVAL (NULL, bad range), ERANGE (a sequence longer than 32767:
+ *   the exact keys of this path need the shorter lengths), ENOMEM, ECUDA.
+ */
+int famsa_msf_rows(const famsa_family *f, int32_t row_begin, int32_t row_end, int32_t *edge_a,
+                   int32_t *edge_b, uint64_t *h_num, uint32_t *h_den, int out_on_device,
+                   void *cuda_stream);
+
+/*
+ * famsa_tree_from_edges -- the single-linkage tree of k points from any edge
+ * list that contains a minimum spanning tree of their distance graph (for
+ * example the union of the famsa_msf_rows forests of shards that cover rows
+ * [1, k)).  Edges as famsa_msf_rows writes them: points 0..k-1, distances as
+ * fractions with a denominator <= 32767 and a numerator below 2^32, or +inf.
+ * Outputs as famsa_slink_tree (pi, lambda, merge list, sizes), in the labels
+ * of the edges.  All buffers on the device iff on_device != 0; the call
+ * waits for its stream.
+ * Errors: EINVAL (k < 1, NULL, fewer than k - 1 edges, an edge that is out
+ *   of range, a self loop, a distance outside the range above, or edges that
+ *   do not join all k points; outputs then undefined), ENOMEM, ECUDA.
+ */
+int famsa_tree_from_edges(int32_t k, int64_t n_edges, const int32_t *edge_a, const int32_t *edge_b,
+                          const uint64_t *e_num, const uint32_t *e_den, int32_t *pi,
+                          uint64_t *lambda_num, uint32_t *lambda_den, int32_t *merges,
+                          uint64_t *h_num, uint32_t *h_den, int32_t *sizes, int on_device,
+                          void *cuda_stream);
+
+/*
  * famsa_merge_similarity -- the merge heights as the paper's similarity
  * LCS / indel^2 ("Pairwise similarities calculation"), a double beside the
  * exact fractions the tree calls return.  A height num / den is the distance

@@ -27,6 +27,10 @@ Functions and the paper passages they follow (FAMSA, Methods):
   bit-parallel rows, resumable over ranges of points, for families too large
   for the DP (the k=400,000 digest).
 * :func:`merges` -- the merge list with the fixed (lambda, index) order.
+* :func:`msf_rows`, :func:`slink_edges`, :func:`tree_from_edges` -- the
+  sharded pair set: Kruskal's minimum spanning forest of a range of rows, and
+  SLINK over an edge list alone (single linkage depends only on a minimum
+  spanning tree).
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against brute
 force, closed forms, invariants, textbook examples or library routines.
@@ -80,6 +84,8 @@ def _load():
             "oracle_slink_bitpar_range": ([_P, _P, i32, i32, i32, _P, _P, _P, ctypes.c_int],
                                           ctypes.c_int),
             "oracle_reduce_keys": ([_P, _P, i64, _P, _P], ctypes.c_int),
+            "oracle_msf_rows": ([_P, _P, i32, _P, i32, i32, _P, _P, _P, _P, ctypes.c_int], i64),
+            "oracle_slink_edges": ([i32, i64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
             "oracle_lcs_allpairs": ([_P, _P, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_lcs_rows": ([_P, _P, i32, i32, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_slink_matrix": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
@@ -325,6 +331,43 @@ def merges(pi, lnum, lden):
 def tree(residues, offsets, nthreads: int = 0):
     """Full oracle result for a family: dict with pi, lambda, merges (streamed SLINK)."""
     pi, ln, ld = slink_streamed(residues, offsets, nthreads)
+    pairs, hn, hd, sz = merges(pi, ln, ld)
+    return {"pi": pi, "lambda_num": ln, "lambda_den": ld, "merges": pairs, "h_num": hn,
+            "h_den": hd, "sizes": sz}
+
+
+# --------------------------------------------------------------------- shards
+def msf_rows(residues, offsets, r0: int, r1: int, order=None, nthreads: int = 0):
+    """Kruskal's minimum spanning forest of the pairs (order[i], order[j]), r0 <= i < r1,
+    j < i: dict of edge_a < edge_b (labels), h_num / h_den (reduced keys)."""
+    res, off, k = _prep(residues, offsets)
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    n = max(r1 - 1, 0) if r1 > 0 else 0
+    ea = np.empty(max(n, 1), np.int32)
+    eb = np.empty(max(n, 1), np.int32)
+    en = np.empty(max(n, 1), np.uint64)
+    ed = np.empty(max(n, 1), np.uint32)
+    got = _load().oracle_msf_rows(_ptr(res), _ptr(off), k, None if o is None else _ptr(o), r0, r1,
+                                  _ptr(ea), _ptr(eb), _ptr(en), _ptr(ed), nthreads)
+    _check(0 if got >= 0 else got, "oracle_msf_rows")
+    return {"edge_a": ea[:got], "edge_b": eb[:got], "h_num": en[:got], "h_den": ed[:got]}
+
+
+def slink_edges(k: int, edges: dict):
+    """SLINK over an edge list alone (+inf for absent pairs): (pi, lambda_num, lambda_den)."""
+    ea = np.ascontiguousarray(edges["edge_a"], dtype=np.int32)
+    eb = np.ascontiguousarray(edges["edge_b"], dtype=np.int32)
+    en = np.ascontiguousarray(edges["h_num"], dtype=np.uint64)
+    ed = np.ascontiguousarray(edges["h_den"], dtype=np.uint32)
+    pi, ln, ld = _tree_out(k)
+    _check(_load().oracle_slink_edges(k, len(ea), _ptr(ea), _ptr(eb), _ptr(en), _ptr(ed), _ptr(pi),
+                                      _ptr(ln), _ptr(ld)), "oracle_slink_edges")
+    return pi, ln, ld
+
+
+def tree_from_edges(k: int, edges: dict):
+    """Full tree result (pi, lambda, merge list) from an edge list alone."""
+    pi, ln, ld = slink_edges(k, edges)
     pairs, hn, hd, sz = merges(pi, ln, ld)
     return {"pi": pi, "lambda_num": ln, "lambda_den": ld, "merges": pairs, "h_num": hn,
             "h_den": hd, "sizes": sz}

@@ -696,3 +696,122 @@ int oracle_merges(const int32_t *pi, const uint64_t *lnum, const uint32_t *lden,
   free(ord); free(tmp); free(parent); free(cid); free(csize);
   return 0;
 }
+
+/* ------------------------------------------------------------ sharded pair sets */
+/*
+ * Minimum spanning forest of the pairs (order[i], order[j]) with r0 <= i < r1
+ * and j < i (order: a permutation of 0..k-1, the row order of the shard; NULL
+ * means the identity), by Kruskal's algorithm: every such pair's exact key
+ * by the DP, the pairs sorted by (key, smaller label, larger label), and each
+ * pair taken when its points are not yet joined.  Writes the forest's edges
+ * (a < b, reduced fractions) and returns their number, or a negative value.
+ * Used for the sharded tree ("Pairwise similarities calculation" spreads the
+ * pairs; single linkage depends only on a minimum spanning tree).
+ */
+typedef struct { okey key; int32_t a, b; } oedge;
+static int edge_lt(const oedge *x, const oedge *y) {
+  if (key_lt(x->key, y->key)) return 1;
+  if (key_lt(y->key, x->key)) return 0;
+  if (x->a != y->a) return x->a < y->a;
+  return x->b < y->b;
+}
+static void esort(oedge *v, oedge *tmp, int64_t n) {
+  if (n < 2) return;
+  int64_t h = n / 2;
+  esort(v, tmp, h);
+  esort(v + h, tmp, n - h);
+  int64_t i = 0, j = h, t = 0;
+  while (i < h && j < n) tmp[t++] = edge_lt(&v[j], &v[i]) ? v[j++] : v[i++];
+  while (i < h) tmp[t++] = v[i++];
+  while (j < n) tmp[t++] = v[j++];
+  memcpy(v, tmp, sizeof(oedge) * (size_t)n);
+}
+
+int64_t oracle_msf_rows(const uint8_t *res, const int64_t *off, int32_t k, const int32_t *order,
+                        int32_t r0, int32_t r1, int32_t *ea, int32_t *eb, uint64_t *enum_,
+                        uint32_t *eden, int nthreads) {
+  if (k < 1 || r0 < 0 || r1 > k || r0 > r1) return -1;
+  set_threads(nthreads);
+  int64_t m = ((int64_t)r1 * (r1 - 1) - (int64_t)r0 * (r0 - 1)) / 2;
+  oedge *E = (oedge *)malloc(sizeof(oedge) * (size_t)(m > 0 ? m : 1));
+  oedge *T = (oedge *)malloc(sizeof(oedge) * (size_t)(m > 0 ? m : 1));
+  int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t ml = max_len(off, k);
+  if (!E || !T || !parent) { free(E); free(T); free(parent); return -2; }
+  int bad = 0;
+#pragma omp parallel
+  {
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ml + 1));
+    if (!row) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = r0; i < r1; ++i) {
+      if (!row) continue;
+      int64_t base = ((int64_t)i * (i - 1) - (int64_t)r0 * (r0 - 1)) / 2;
+      int32_t x = order ? order[i] : i;
+      int32_t lx = (int32_t)(off[x + 1] - off[x]);
+      for (int32_t j = 0; j < i; ++j) {
+        int32_t y = order ? order[j] : j;
+        int32_t ly = (int32_t)(off[y + 1] - off[y]);
+        int32_t L = lcs_dp(res + off[x], lx, res + off[y], ly, row);
+        oedge e;
+        e.key = key_from_lcs(L, lx, ly);
+        e.a = x < y ? x : y;
+        e.b = x < y ? y : x;
+        E[base + j] = e;
+      }
+    }
+    free(row);
+  }
+  if (bad) { free(E); free(T); free(parent); return -2; }
+  esort(E, T, m);
+  for (int32_t v = 0; v < k; ++v) parent[v] = v;
+  int64_t n = 0;
+  for (int64_t t = 0; t < m; ++t) {
+    int32_t x = uf_find(parent, E[t].a), y = uf_find(parent, E[t].b);
+    if (x == y) continue;
+    parent[x] = y;
+    ea[n] = E[t].a;
+    eb[n] = E[t].b;
+    key_reduce(E[t].key, &enum_[n], &eden[n]);
+    ++n;
+  }
+  free(E); free(T); free(parent);
+  return n;
+}
+
+/*
+ * Single linkage of k points from an edge list alone: Sibson's SLINK over the
+ * k x k matrix whose entries are the given edges' keys and +inf elsewhere
+ * (the lightest key when an edge repeats).  When the edges contain a minimum
+ * spanning tree of the complete distance graph, the single-link distances,
+ * and so pi and lambda, are those of the complete graph.
+ */
+typedef struct { const okey *D; int32_t k; } dense_ctx;
+static void dense_row(void *c, int32_t n, okey *M) {
+  dense_ctx *t = (dense_ctx *)c;
+  for (int32_t j = 0; j < n; ++j) M[j] = t->D[(size_t)j * t->k + n];
+}
+
+int oracle_slink_edges(int32_t k, int64_t m, const int32_t *ea, const int32_t *eb,
+                       const uint64_t *enum_, const uint32_t *eden, int32_t *pi, uint64_t *lnum,
+                       uint32_t *lden) {
+  if (k < 1 || m < 0) return -1;
+  okey *D = (okey *)malloc(sizeof(okey) * (size_t)k * (size_t)k);
+  if (!D) return -2;
+  for (size_t t = 0; t < (size_t)k * k; ++t) D[t] = KEY_INF;
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t a = ea[e], b = eb[e];
+    if (a < 0 || b < 0 || a >= k || b >= k || a == b) { free(D); return -1; }
+    okey q = {enum_[e], eden[e]};
+    if (q.den == 0) q = KEY_INF;
+    D[(size_t)a * k + b] = key_min(D[(size_t)a * k + b], q);
+    D[(size_t)b * k + a] = D[(size_t)a * k + b];
+  }
+  dense_ctx c = {D, k};
+  int rc = slink_core(k, dense_row, &c, pi, lnum, lden);
+  free(D);
+  return rc;
+}

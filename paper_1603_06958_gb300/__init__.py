@@ -99,6 +99,10 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_alloc_count": ([], ctypes.c_int64),
             "famsa_merge_similarity": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
+            "famsa_msf_rows": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, _P],
+                               ctypes.c_int),
+            "famsa_tree_from_edges": ([ctypes.c_int32, ctypes.c_int64] + [_P] * 11 + [ctypes.c_int, _P],
+                                      ctypes.c_int),
             "famsa_debug_set_serial": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
@@ -332,6 +336,50 @@ def famsa_slink_tree(fam: Family, device: bool = False, stream=None) -> dict:
 
 
 slink_tree = famsa_slink_tree
+
+
+def famsa_msf_rows(fam: Family, row_begin: int, row_end: int, device: bool = False,
+                   stream=None) -> dict:
+    """Minimum spanning tree of the pairs of rows [row_begin, row_end) (one shard of
+    the pair set): row_end - 1 edges, dict of edge_a < edge_b, h_num / h_den."""
+    n = max(row_end - 1, 0)
+    out = {"edge_a": _empty(n, np.int32, device), "edge_b": _empty(n, np.int32, device),
+           "h_num": _empty(n, np.uint64, device), "h_den": _empty(n, np.uint32, device)}
+    _check(load().famsa_msf_rows(fam.handle, row_begin, row_end, _ptr(out["edge_a"])[0],
+                                 _ptr(out["edge_b"])[0], _ptr(out["h_num"])[0], _ptr(out["h_den"])[0],
+                                 int(device), _stream_ptr(stream)), "famsa_msf_rows")
+    return out
+
+
+msf_rows = famsa_msf_rows
+
+
+def famsa_tree_from_edges(k: int, edges: dict, device: bool = False, stream=None) -> dict:
+    """The single-linkage tree of k points from an edge list that contains a minimum
+    spanning tree (e.g. the union of famsa_msf_rows forests of all shards)."""
+    m = len(edges["edge_a"])
+    _require(edges["edge_a"], np.int32, "edge_a")
+    _require(edges["edge_b"], np.int32, "edge_b", count=m)
+    _require(edges["h_num"], np.uint64, "h_num", count=m)
+    _require(edges["h_den"], np.uint32, "h_den", count=m)
+    sides = {_ptr(edges[n])[1] for n in ("edge_a", "edge_b", "h_num", "h_den")}
+    if sides != {bool(device)}:
+        raise ValueError("edges must be on the %s" % ("device" if device else "host"))
+    km = max(k - 1, 0)
+    out = {"pi": _empty(k, np.int32, device), "lambda_num": _empty(k, np.uint64, device),
+           "lambda_den": _empty(k, np.uint32, device), "merges": _empty(2 * km, np.int32, device),
+           "h_num": _empty(km, np.uint64, device), "h_den": _empty(km, np.uint32, device),
+           "sizes": _empty(km, np.int32, device)}
+    ins = [_ptr(edges[n])[0] for n in ("edge_a", "edge_b", "h_num", "h_den")]
+    outs = [_ptr(out[n])[0] for n in ("pi", "lambda_num", "lambda_den", "merges", "h_num", "h_den",
+                                      "sizes")]
+    _check(load().famsa_tree_from_edges(k, m, *ins, *outs, int(device), _stream_ptr(stream)),
+           "famsa_tree_from_edges")
+    out["merges"] = out["merges"].reshape(km, 2)
+    return out
+
+
+tree_from_edges = famsa_tree_from_edges
 
 
 class Batch:

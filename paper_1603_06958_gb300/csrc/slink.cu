@@ -27,25 +27,6 @@ static int g_update_path = 0;
 static int g_row_block = 0;  // rows per row block (0 automatic)
 static int g_serial = 0;       // 1: no overlap of LCS and row update (timing studies)
 
-struct Scratch {
-  std::vector<void *> ptrs;
-  cudaStream_t st;
-  cudaError_t err = cudaSuccess;
-  template <typename T>
-  T *get(size_t n) {
-    void *p = nullptr;
-    if (err != cudaSuccess) return nullptr;
-    err = lib_malloc_async(&p, std::max<size_t>(n, 1) * sizeof(T), st);
-    if (err != cudaSuccess) return nullptr;
-    ptrs.push_back(p);
-    return static_cast<T *>(p);
-  }
-  void release() {
-    for (void *p : ptrs) cudaFreeAsync(p, st);
-    ptrs.clear();
-  }
-};
-
 int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_out,
                int32_t *merges_out, uint64_t *hnum_out, uint32_t *hden_out, int32_t *sizes_out,
                bool out_on_device, cudaStream_t st) {
@@ -170,19 +151,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     for (int32_t s = 0; s < k; ++s) { h_iota[s] = s; h_w[s] = (f->h_slen[s] + 63) / 64; }
     int32_t *d_iota = sc.get<int32_t>(k);
     // finalisation buffers
-    const size_t lv = fin_levels(k);
-    FinBufs FB;
-    FB.idx = sc.get<int32_t>(k); FB.posof = sc.get<int32_t>(k);
-    FB.it = sc.get<int32_t>(lv * k); FB.rt = sc.get<int32_t>(lv * k);
-    FB.gt = sc.get<uint64_t>(lv * k);
-    FB.pi = sc.get<int32_t>(k); FB.sub_lo = sc.get<int32_t>(k); FB.sub_hi = sc.get<int32_t>(k);
-    FB.ordA = sc.get<int32_t>(k); FB.ordB = sc.get<int32_t>(k); FB.rank = sc.get<int32_t>(k);
-    FB.sorder = sc.get<int32_t>(k); FB.merges = sc.get<int32_t>(2 * (size_t)k);
-    FB.sizes = sc.get<int32_t>(k);
-    FB.lam = sc.get<uint64_t>(k); FB.hkey = sc.get<uint64_t>(k);
-    FB.lnum = sc.get<uint64_t>(k); FB.hnum = sc.get<uint64_t>(k);
-    FB.lden = sc.get<uint32_t>(k); FB.hden = sc.get<uint32_t>(k);
-    FB.sz = sc.get<int64_t>(k); FB.szpre = sc.get<int64_t>(k); FB.tot = sc.get<int64_t>(2);
+    FinBufs FB = alloc_fin_bufs(sc, k);
     if (sc.err != cudaSuccess) { err = sc.err; goto done; }
     CKE(cudaMemcpyAsync(d_iota, h_iota.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
     if (msf) {

@@ -340,6 +340,46 @@ struct FinBufs {
 };
 
 size_t fin_levels(int32_t k);
+
+// Stream-ordered scratch of one call: every get() allocates on st (through
+// lib_malloc_async); release() frees all of it on st.  The first failure is
+// kept in err and later gets return nullptr.
+struct Scratch {
+  std::vector<void *> ptrs;
+  cudaStream_t st = nullptr;
+  cudaError_t err = cudaSuccess;
+  template <typename T>
+  T *get(size_t n) {
+    void *p = nullptr;
+    if (err != cudaSuccess) return nullptr;
+    err = lib_malloc_async(&p, (n > 0 ? n : 1) * sizeof(T), st);
+    if (err != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return static_cast<T *>(p);
+  }
+  void release() {
+    for (void *p : ptrs) cudaFreeAsync(p, st);
+    ptrs.clear();
+  }
+};
+
+// the finalisation's buffers for k points
+inline FinBufs alloc_fin_bufs(Scratch &sc, int32_t k) {
+  const size_t lv = fin_levels(k);
+  FinBufs FB;
+  FB.idx = sc.get<int32_t>(k); FB.posof = sc.get<int32_t>(k);
+  FB.it = sc.get<int32_t>(lv * k); FB.rt = sc.get<int32_t>(lv * k);
+  FB.gt = sc.get<uint64_t>(lv * k);
+  FB.pi = sc.get<int32_t>(k); FB.sub_lo = sc.get<int32_t>(k); FB.sub_hi = sc.get<int32_t>(k);
+  FB.ordA = sc.get<int32_t>(k); FB.ordB = sc.get<int32_t>(k); FB.rank = sc.get<int32_t>(k);
+  FB.sorder = sc.get<int32_t>(k); FB.merges = sc.get<int32_t>(2 * (size_t)k);
+  FB.sizes = sc.get<int32_t>(k);
+  FB.lam = sc.get<uint64_t>(k); FB.hkey = sc.get<uint64_t>(k);
+  FB.lnum = sc.get<uint64_t>(k); FB.hnum = sc.get<uint64_t>(k);
+  FB.lden = sc.get<uint32_t>(k); FB.hden = sc.get<uint32_t>(k);
+  FB.sz = sc.get<int64_t>(k); FB.szpre = sc.get<int64_t>(k); FB.tot = sc.get<int64_t>(2);
+  return FB;
+}
 cudaError_t launch_finalize(const int32_t *ord, uint64_t *gap, const int32_t *perm, int32_t k,
                             FinBufs &B, cudaStream_t st, int64_t *launches, bool widen);
 cudaError_t launch_slink_global(const SlinkState &S, const uint16_t *rowbuf, int64_t ld, int32_t r0,

@@ -347,6 +347,15 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
     par[v] = (I)v; head[v] = (I)v; tail[v] = (I)v; nxt[v] = (I)v; size[v] = (I)1;
   }
   __syncthreads();
+  if (*err) {
+    // an unfinished tree: leave an in-bounds placeholder order for the
+    // kernels that follow (the call reports the error)
+    for (int32_t p = threadIdx.x; p < k; p += kKrtThreads) {
+      ord[p] = p;
+      if (p + 1 < k) gi[p] = 0;
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
   int32_t root = 0;
   for (int32_t c0 = 0; c0 < k - 1; c0 += kKrtChunk) {
@@ -361,6 +370,7 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
         const int32_t j = jb + lane;
         if (j < cn) {
           int32_t x = ca[j], y = cb[j];
+          if (x < 0 || x >= k || y < 0 || y >= k) { x = 0; y = 0; }  // out of range: reported as a self join
           for (int it = 0; it < 64 && (int32_t)par[x] != x; ++it) x = par[x];
           for (int it = 0; it < 64 && (int32_t)par[y] != y; ++it) y = par[y];
           sx[lane] = x;
@@ -373,7 +383,7 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
             int32_t x = sx[l], y = sy[l];
             while ((int32_t)par[x] != x) x = par[x];  // links added by the joins since the lookup
             while ((int32_t)par[y] != y) y = par[y];
-            if (x == y) { *err |= 4; break; }
+            if (x == y) { *err |= 4; break; }  // two points already joined: not a tree
             const I tx = tail[x], hy = head[y], hx = head[x], ty = tail[y];
             const I sxz = size[x], syz = size[y];
             gidx[tx] = c0 + jb + l;
@@ -390,7 +400,15 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && *err == 0) {
+  __syncthreads();
+  if (*err) {
+    for (int32_t p = threadIdx.x; p < k; p += kKrtThreads) {
+      ord[p] = p;
+      if (p + 1 < k) gi[p] = 0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
     int32_t v = head[root];
     for (int32_t p = 0; p < k; ++p) {
       ord[p] = v;
@@ -407,7 +425,7 @@ __global__ void __launch_bounds__(kKrtThreads) k_msf_krt_smem(int32_t k, const i
                                                               int32_t *ctl) {
   extern __shared__ int32_t krt_sm[];
   __shared__ int32_t err, sx[32], sy[32];
-  if (threadIdx.x == 0) err = 0;
+  if (threadIdx.x == 0) err = ctl[kMsfErr] ? 16 : 0;
   int32_t *ca = krt_sm, *cb = ca + kKrtChunk;
   uint16_t *par = reinterpret_cast<uint16_t *>(cb + kKrtChunk);
   uint16_t *head = par + k, *tail = head + k, *nxt = tail + k, *size = nxt + k;
@@ -420,10 +438,63 @@ __global__ void __launch_bounds__(kKrtThreads) k_msf_krt_global(int32_t k, const
                                                                 int32_t *gi, int32_t *ctl) {
   __shared__ int32_t ca[kKrtChunk], cb[kKrtChunk];
   __shared__ int32_t err, sx[32], sy[32];
-  if (threadIdx.x == 0) err = 0;
+  if (threadIdx.x == 0) err = ctl[kMsfErr] ? 16 : 0;
   const int64_t K = k;
   krt_run<int32_t>(k, ea, eb, w, w + K, w + 2 * K, w + 3 * K, w + 4 * K, gidx, ord, gi, &err, ca, cb, sx, sy);
   if (threadIdx.x == 0 && err) atomicOr(&ctl[kMsfErr], err);
+}
+
+
+// ---- edge lists in and out (sharded pair sets)
+
+__global__ void k_msf_no_candidates(MsfState S, int32_t n) {
+  const int32_t v = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (v < n) S.ckey[v] = kMsfNone;
+}
+
+// caller edges (a, b, num / den) -> tree edges with order-code keys; a bad
+// endpoint, a self loop or a distance outside the order codes' range sets
+// error bit 8
+__global__ void k_msf_from_fractions(int32_t m, int32_t k, const int32_t *a, const int32_t *b,
+                                     const uint64_t *num, const uint32_t *den, uint64_t *mkey, int32_t *ma,
+                                     int32_t *mb, int32_t *ctl) {
+  const int32_t e = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (e >= m) return;
+  int32_t x = a[e], y = b[e];
+  const uint64_t p = num[e];
+  const uint32_t q = den[e];
+  const bool ok = x >= 0 && y >= 0 && x < k && y < k && x != y && (q == 0 || (q <= 32767 && p < (1ull << 32)));
+  if (!ok) {
+    atomicOr(&ctl[kMsfErr], 8);
+    x = 0;
+    y = 1 % k;
+  }
+  ma[e] = min(x, y);
+  mb[e] = max(x, y);
+  mkey[e] = q == 0 ? kMsfInf : order_code((uint32_t)p, q);
+}
+
+// tree edges -> caller labels (through perm, or as they are when perm is
+// null), a < b, and the distance as a reduced fraction (+inf = 1 / 0)
+__global__ void k_msf_to_fractions(int32_t m, const uint64_t *mkey, const int32_t *ma, const int32_t *mb,
+                                   const int32_t *perm, int32_t *a, int32_t *b, uint64_t *num, uint32_t *den) {
+  const int32_t e = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (e >= m) return;
+  int32_t x = ma[e], y = mb[e];
+  if (perm) { x = perm[x]; y = perm[y]; }
+  a[e] = min(x, y);
+  b[e] = max(x, y);
+  const uint64_t key = mkey[e];
+  if (key == kMsfInf) {
+    num[e] = 1;
+    den[e] = 0;
+  } else {
+    uint64_t p;
+    uint32_t q;
+    code_fraction(key, &p, &q);
+    num[e] = p;
+    den[e] = q;
+  }
 }
 
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)std::max<int64_t>((n + t - 1) / t, 1); }
@@ -460,6 +531,41 @@ cudaError_t launch_msf_block(MsfState &S, const uint16_t *rowbuf, int64_t ld, in
   std::swap(S.ma, S.na);
   std::swap(S.mb, S.nb);
   if (launches) *launches += L;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_msf_edges(MsfState &S, int32_t n, int32_t m, cudaStream_t st, int64_t *launches) {
+  const int T = 256;
+  int64_t L = 0;
+  k_msf_begin<<<nblocks(n, T), T, 0, st>>>(S, n);
+  k_msf_no_candidates<<<nblocks(n, T), T, 0, st>>>(S, n);
+  L += 2;
+  const int rounds = msf_rounds(n);
+  for (int r = 0; r < rounds; ++r) {
+    k_msf_cmin<false><<<nblocks((int64_t)n + m, T), T, 0, st>>>(S, n, n, m);
+    k_msf_cmin<true><<<nblocks((int64_t)n + m, T), T, 0, st>>>(S, n, n, m);
+    k_msf_hook<<<nblocks(n, T), T, 0, st>>>(S, n);
+    k_msf_jump<<<nblocks(n, T), T, 0, st>>>(S, n);
+    L += 4;
+  }
+  k_msf_end<<<1, 1, 0, st>>>(S, n);
+  ++L;
+  std::swap(S.mkey, S.nkey);
+  std::swap(S.ma, S.na);
+  std::swap(S.mb, S.nb);
+  if (launches) *launches += L;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_msf_from_fractions(MsfState &S, int32_t m, int32_t k, const int32_t *a, const int32_t *b,
+                                      const uint64_t *num, const uint32_t *den, cudaStream_t st) {
+  if (m > 0) k_msf_from_fractions<<<nblocks(m, 256), 256, 0, st>>>(m, k, a, b, num, den, S.mkey, S.ma, S.mb, S.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_msf_to_fractions(const MsfState &S, int32_t m, const int32_t *perm, int32_t *a, int32_t *b,
+                                    uint64_t *num, uint32_t *den, cudaStream_t st) {
+  if (m > 0) k_msf_to_fractions<<<nblocks(m, 256), 256, 0, st>>>(m, S.mkey, S.ma, S.mb, perm, a, b, num, den);
   return cudaGetLastError();
 }
 

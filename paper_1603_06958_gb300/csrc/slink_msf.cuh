@@ -37,5 +37,16 @@ cudaError_t launch_msf_leaf_order(const MsfState &S, int32_t k, int32_t *ord, ui
                                   int32_t *idx_b, int32_t *work, uint64_t *ek, cudaStream_t st,
                                   int64_t *launches);
 int msf_rounds(int32_t r1);
+// The minimum spanning tree of points [0, n) from an edge list alone: the m
+// edges in S.mkey/ma/mb (a graph that connects all n points) -> the n - 1
+// tree edges, swapped into S.mkey/ma/mb.
+cudaError_t launch_msf_edges(MsfState &S, int32_t n, int32_t m, cudaStream_t st, int64_t *launches);
+// Caller edge lists <-> tree edges: distances as reduced fractions num / den
+// (+inf = 1 / 0) on the caller's side, order codes inside; perm (optional)
+// maps tree labels to the caller's on the way out.
+cudaError_t launch_msf_from_fractions(MsfState &S, int32_t m, int32_t k, const int32_t *a, const int32_t *b,
+                                      const uint64_t *num, const uint32_t *den, cudaStream_t st);
+cudaError_t launch_msf_to_fractions(const MsfState &S, int32_t m, const int32_t *perm, int32_t *a, int32_t *b,
+                                    uint64_t *num, uint32_t *den, cudaStream_t st);
 
 }  // namespace famsa
