@@ -168,6 +168,69 @@ int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_of
                     void *cuda_stream);
 
 /*
+ * famsa_progressive_schedule -- the merge list in the form the progressive
+ * stage consumes ("Progressive construction of the alignment": O(k) profile
+ * alignments in guide-tree order, spread over threads; at least half align a
+ * single sequence with a profile, a simpler DP).
+ *   merges (2(k-1)), sizes (k-1): as famsa_slink_tree / famsa_batch_tree
+ *     write them (merge t joins ids merges[2t], merges[2t+1]; ids < k are
+ *     sequences, k + t' the cluster made by merge t').
+ *   level[t] (k-1): 1 + the larger level of merge t's two children (a
+ *     sequence is level 0).  Merges of one level never use one another, so
+ *     a level can run at once after the levels below it.
+ *   order (k-1): the merges sorted by (level, t).
+ *   level_start (k entries of room): level l is order[level_start[l-1] ..
+ *     level_start[l]), l = 1..n_levels.
+ *   kind[t] (k-1): 0 two single sequences, 1 a single sequence and a
+ *     profile (the degenerate case), 2 two profiles.
+ *   n_levels: host int32, the number of levels.
+ * All other buffers on the device iff on_device != 0; the call waits for its
+ * stream.
+ * Errors: EINVAL (k < 1, NULL, a child id that is not a sequence or an
+ *   earlier merge), ENOMEM, ECUDA.
+ */
+int famsa_progressive_schedule(int32_t k, const int32_t *merges, const int32_t *sizes, int32_t *level,
+                               int32_t *order, int32_t *level_start, int32_t *kind,
+                               int32_t *n_levels, int on_device, void *cuda_stream);
+
+/*
+ * Gap types and set-size scaled gap costs ("Gap types and costs
+ * determination").  Four gap types with affine costs: terminal open (T_o),
+ * terminal extension (T_e), open (G_o), extension (G_e); every cost is
+ * multiplied by g_scale = 1 + log(k / g_l) / g_d (natural log; the paper's
+ * defaults g_l = 45, g_d = 7), k the number of sequences of the input set.
+ * Alignments are m rows of n bytes: residue codes, or FAMSA_GAP for a gap.
+ * Type codes: 0 residue, 1 T_o, 2 T_e, 3 G_o, 4 G_e.  A gap before a row's
+ * first residue or after its last is terminal, any other is not; the first
+ * gap of a run opens it and the others extend it (a row of gaps only is one
+ * terminal run).
+ *
+ * famsa_gap_types: those types for every cell (aln, types: m*n bytes ON THE
+ *   DEVICE; stream-ordered).
+ * famsa_gap_scale: g_scale for a set of k sequences (host; NaN for k < 1,
+ *   g_l <= 0 or g_d == 0).
+ * famsa_gap_cost: per row, g_scale(k) * (T_o*#T_o + T_e*#T_e + G_o*#G_o +
+ *   G_e*#G_e), costs = {T_o, T_e, G_o, G_e} on the host, types and cost (m
+ *   doubles) ON THE DEVICE; stream-ordered.
+ * famsa_gap_insert: c gap columns inserted before original columns
+ *   positions[0..c) (host, ascending, 0..n; equal positions give adjacent
+ *   columns) into every row, with the types corrected as the paper's six
+ *   cases S1..S6 say: the inserted gap takes its type from its neighbours,
+ *   and a T_o or G_o right after it becomes T_e or G_e.  aln, types: m*n,
+ *   aln_out, types_out: m*(n+c) bytes, ON THE DEVICE; the call waits for its
+ *   stream.
+ * Errors: EINVAL (NULL, negative sizes, positions out of range or not
+ *   ascending), ERANGE (more than 2^31-1 rows for famsa_gap_types), ECUDA.
+ */
+#define FAMSA_GAP 255
+int famsa_gap_types(const uint8_t *aln, int64_t m, int32_t n, uint8_t *types, void *cuda_stream);
+double famsa_gap_scale(int64_t k, double g_l, double g_d);
+int famsa_gap_cost(const uint8_t *types, int64_t m, int32_t n, int64_t k, const double *costs, double g_l,
+                   double g_d, double *cost, void *cuda_stream);
+int famsa_gap_insert(const uint8_t *aln, const uint8_t *types, int64_t m, int32_t n, const int32_t *positions,
+                     int32_t c, uint8_t *aln_out, uint8_t *types_out, void *cuda_stream);
+
+/*
  * Sharding the pair set across devices ("Pairwise similarities calculation":
  * the pairs are independent; "Determination of the guide tree": single
  * linkage).  Single linkage depends only on a minimum spanning tree of the

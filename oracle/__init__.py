@@ -27,6 +27,12 @@ Functions and the paper passages they follow (FAMSA, Methods):
   bit-parallel rows, resumable over ranges of points, for families too large
   for the DP (the k=400,000 digest).
 * :func:`merges` -- the merge list with the fixed (lambda, index) order.
+* :func:`gap_types`, :func:`gap_insert`, :func:`gap_scale`, :func:`gap_cost`
+  -- the four gap types, gap-column insertion with the six corrections, and
+  the set-size gap-cost scaling ("Gap types and costs determination").
+* :func:`schedule` -- the merge list as the progressive stage's schedule
+  (levels of independent merges, their order, and which merges align a
+  single sequence) ("Progressive construction of the alignment").
 * :func:`msf_rows`, :func:`slink_edges`, :func:`tree_from_edges` -- the
   sharded pair set: Kruskal's minimum spanning forest of a range of rows, and
   SLINK over an edge list alone (single linkage depends only on a minimum
@@ -58,7 +64,7 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
             tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-            cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC]
+            cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
             try:
                 subprocess.check_call(cmd)
             except subprocess.CalledProcessError:
@@ -86,6 +92,11 @@ def _load():
             "oracle_reduce_keys": ([_P, _P, i64, _P, _P], ctypes.c_int),
             "oracle_msf_rows": ([_P, _P, i32, _P, i32, i32, _P, _P, _P, _P, ctypes.c_int], i64),
             "oracle_slink_edges": ([i32, i64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+            "oracle_schedule": ([i32, _P, _P, _P, _P, _P, _P], i32),
+            "oracle_gap_types": ([_P, i64, i32, _P], ctypes.c_int),
+            "oracle_gap_insert": ([_P, _P, i64, i32, _P, i32, _P, _P], ctypes.c_int),
+            "oracle_gap_scale": ([i64, ctypes.c_double, ctypes.c_double], ctypes.c_double),
+            "oracle_gap_cost": ([_P, i64, i32, i64, _P, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
             "oracle_lcs_allpairs": ([_P, _P, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_lcs_rows": ([_P, _P, i32, i32, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_slink_matrix": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
@@ -371,3 +382,60 @@ def tree_from_edges(k: int, edges: dict):
     pairs, hn, hd, sz = merges(pi, ln, ld)
     return {"pi": pi, "lambda_num": ln, "lambda_den": ld, "merges": pairs, "h_num": hn,
             "h_den": hd, "sizes": sz}
+
+
+# --------------------------------------------------------------------- schedule
+def schedule(merges, sizes):
+    """Progressive-stage schedule of a merge list: dict of level, order, level_start, kind."""
+    mg = np.ascontiguousarray(np.asarray(merges).reshape(-1), dtype=np.int32)
+    sz = np.ascontiguousarray(sizes, dtype=np.int32)
+    n = len(sz)
+    k = n + 1
+    level = np.empty(max(n, 1), np.int32)
+    order = np.empty(max(n, 1), np.int32)
+    start = np.empty(max(n, 1) + 1, np.int32)
+    kind = np.empty(max(n, 1), np.int32)
+    top = _load().oracle_schedule(k, _ptr(mg), _ptr(sz), _ptr(level), _ptr(order), _ptr(start),
+                                  _ptr(kind))
+    _check(0 if top >= 0 else top, "oracle_schedule")
+    return {"level": level[:n], "order": order[:n], "level_start": start[:top + 1], "kind": kind[:n],
+            "n_levels": int(top)}
+
+
+# --------------------------------------------------------------------- gaps
+GAP = 255
+
+
+def gap_types(aln):
+    """Per-cell gap types of an m x n alignment (0 residue, 1 T_o, 2 T_e, 3 G_o, 4 G_e)."""
+    a = np.ascontiguousarray(aln, dtype=np.uint8)
+    t = np.empty_like(a)
+    _check(_load().oracle_gap_types(_ptr(a), a.shape[0], a.shape[1], _ptr(t)), "oracle_gap_types")
+    return t
+
+
+def gap_insert(aln, types, positions):
+    """Insert gap columns before original columns positions (ascending) with the
+    S1..S6 corrections: (aln_out, types_out)."""
+    a = np.ascontiguousarray(aln, dtype=np.uint8)
+    t = np.ascontiguousarray(types, dtype=np.uint8)
+    p = np.ascontiguousarray(positions, dtype=np.int32)
+    m, n = a.shape
+    ao = np.empty((m, n + len(p)), np.uint8)
+    to = np.empty((m, n + len(p)), np.uint8)
+    _check(_load().oracle_gap_insert(_ptr(a), _ptr(t), m, n, _ptr(p), len(p), _ptr(ao), _ptr(to)),
+           "oracle_gap_insert")
+    return ao, to
+
+
+def gap_scale(k: int, g_l: float = 45.0, g_d: float = 7.0) -> float:
+    return float(_load().oracle_gap_scale(k, g_l, g_d))
+
+
+def gap_cost(types, k: int, costs, g_l: float = 45.0, g_d: float = 7.0):
+    t = np.ascontiguousarray(types, dtype=np.uint8)
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    out = np.empty(t.shape[0], np.float64)
+    _check(_load().oracle_gap_cost(_ptr(t), t.shape[0], t.shape[1], k, _ptr(c), g_l, g_d, _ptr(out)),
+           "oracle_gap_cost")
+    return out

@@ -40,6 +40,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -814,4 +815,143 @@ int oracle_slink_edges(int32_t k, int64_t m, const int32_t *ea, const int32_t *e
   int rc = slink_core(k, dense_row, &c, pi, lnum, lden);
   free(D);
   return rc;
+}
+
+/* ------------------------------------------------------------ progressive schedule */
+/*
+ * The merge list in the form the progressive stage consumes ("Progressive
+ * construction of the alignment": O(k) profile alignments in guide-tree
+ * order, spread over threads; at least half of them align a single sequence
+ * with a profile).  Merge t joins clusters merges[2t] and merges[2t+1]
+ * (ids < k are single sequences, k + t' the result of merge t').
+ *   level[t] = 1 + the larger level of its two children (a sequence is at
+ *     level 0): merges of one level never use one another, so each level can
+ *     run at once, after the levels below it;
+ *   order: the merges sorted by (level, t); level_start[l - 1] .. level_start[l]
+ *     delimit level l in order (level_start has n_levels + 1 entries);
+ *   kind[t]: 0 two single sequences, 1 one sequence and one profile, 2 two
+ *     profiles (a child's size is 1 for a sequence, sizes[t'] for merge t').
+ * Returns n_levels, or a negative value for a bad merge list.
+ */
+int32_t oracle_schedule(int32_t k, const int32_t *merges, const int32_t *sizes, int32_t *level,
+                        int32_t *order, int32_t *level_start, int32_t *kind) {
+  if (k < 1) return -1;
+  int32_t n = k - 1, top = 0;
+  for (int32_t t = 0; t < n; ++t) {
+    int32_t la = 0, lb = 0, sa = 1, sb = 1;
+    int32_t a = merges[2 * t], b = merges[2 * t + 1];
+    if (a < 0 || b < 0 || a >= k + t || b >= k + t) return -1;
+    if (a >= k) { la = level[a - k]; sa = sizes[a - k]; }
+    if (b >= k) { lb = level[b - k]; sb = sizes[b - k]; }
+    level[t] = 1 + (la > lb ? la : lb);
+    kind[t] = (sa > 1) + (sb > 1);
+    if (level[t] > top) top = level[t];
+  }
+  /* counting sort by level, stable in t */
+  for (int32_t l = 0; l <= top; ++l) level_start[l] = 0;
+  for (int32_t t = 0; t < n; ++t) level_start[level[t]]++;
+  int32_t run = 0;
+  for (int32_t l = 1; l <= top; ++l) {
+    int32_t c = level_start[l];
+    level_start[l - 1] = run;
+    run += c;
+  }
+  level_start[top] = run;
+  int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(top + 1));
+  if (!fill) return -2;
+  for (int32_t l = 0; l < top; ++l) fill[l] = level_start[l];
+  for (int32_t t = 0; t < n; ++t) order[fill[level[t] - 1]++] = t;
+  free(fill);
+  return top;
+}
+
+/* ------------------------------------------------------------ gap types and costs */
+/*
+ * "Gap types and costs determination": gaps are terminal open / extension
+ * (T_o = 1, T_e = 2) or open / extension (G_o = 3, G_e = 4); 0 is a residue,
+ * 255 a gap in the alignment rows (m x n bytes).  A gap before the row's
+ * first residue or after its last one is terminal; the first gap of a run
+ * opens it.
+ */
+enum { O_RES = 0, O_TO = 1, O_TE = 2, O_GO = 3, O_GE = 4 };
+int oracle_gap_types(const uint8_t *aln, int64_t m, int32_t n, uint8_t *types) {
+  if (m < 0 || n < 0) return -1;
+  for (int64_t r = 0; r < m; ++r) {
+    const uint8_t *a = aln + r * n;
+    int32_t first = n, last = -1;
+    for (int32_t j = 0; j < n; ++j)
+      if (a[j] != 255) { if (first == n) first = j; last = j; }
+    for (int32_t j = 0; j < n; ++j) {
+      uint8_t t = O_RES;
+      if (a[j] == 255) {
+        int terminal = j < first || j > last;
+        int opens = j == 0 || a[j - 1] != 255;
+        t = terminal ? (opens ? O_TO : O_TE) : (opens ? O_GO : O_GE);
+      }
+      types[r * n + j] = t;
+    }
+  }
+  return 0;
+}
+
+/*
+ * Insertion of gap columns with the six corrections, one inserted gap at a
+ * time from left to right (L: the type left of the new gap, R: the type right
+ * of it, -1 at an end of the row):
+ *   S1 R is T_o: the new gap is T_o and R becomes T_e;
+ *   S2 L is T_e: the new gap is T_e;
+ *   S3 inside (or closing) a run of G_o/G_e: G_e;
+ *   S4 R is G_o: the new gap is G_o and R becomes G_e;
+ *   S5 between residues: G_o;
+ *   S6 L is T_o: the new gap is T_e;
+ * and a gap that starts a new run at an end of the row is T_o.
+ */
+int oracle_gap_insert(const uint8_t *aln, const uint8_t *types, int64_t m, int32_t n, const int32_t *pos,
+                      int32_t c, uint8_t *aln_out, uint8_t *types_out) {
+  if (m < 0 || n < 0 || c < 0) return -1;
+  for (int32_t i = 0; i < c; ++i)
+    if (pos[i] < 0 || pos[i] > n || (i > 0 && pos[i] < pos[i - 1])) return -1;
+  int64_t w = (int64_t)n + c;
+  for (int64_t r = 0; r < m; ++r) {
+    uint8_t *ao = aln_out + r * w, *to = types_out + r * w;
+    /* start from the row as it is, then insert column by column */
+    int64_t len = n;
+    memcpy(ao, aln + r * n, (size_t)n);
+    memcpy(to, types + r * n, (size_t)n);
+    for (int32_t i = 0; i < c; ++i) {
+      int64_t at = pos[i] + i; /* earlier insertions shifted the row */
+      memmove(ao + at + 1, ao + at, (size_t)(len - at));
+      memmove(to + at + 1, to + at, (size_t)(len - at));
+      ++len;
+      int L = at > 0 ? to[at - 1] : -1;
+      int R = at + 1 < len ? to[at + 1] : -1;
+      int g;
+      if (R == O_TO) { g = O_TO; to[at + 1] = O_TE; }                 /* S1 */
+      else if (L == O_TE) g = O_TE;                                    /* S2 */
+      else if (L == O_GO || L == O_GE) g = O_GE;                       /* S3 */
+      else if (R == O_GO) { g = O_GO; to[at + 1] = O_GE; }            /* S4 */
+      else if (L == O_TO) g = O_TE;                                    /* S6 */
+      else if (L < 0 || R < 0) g = O_TO;                               /* new terminal run */
+      else g = O_GO;                                                   /* S5 */
+      ao[at] = 255;
+      to[at] = (uint8_t)g;
+    }
+  }
+  return 0;
+}
+
+/* g_scale = 1 + log(k / g_l) / g_d, and per row g_scale * sum of count x cost */
+double oracle_gap_scale(int64_t k, double g_l, double g_d) { return 1.0 + log((double)k / g_l) / g_d; }
+
+int oracle_gap_cost(const uint8_t *types, int64_t m, int32_t n, int64_t k, const double *costs, double g_l,
+                    double g_d, double *cost) {
+  if (m < 0 || n < 0 || k < 1) return -1;
+  double s = oracle_gap_scale(k, g_l, g_d);
+  for (int64_t r = 0; r < m; ++r) {
+    int64_t cnt[5] = {0, 0, 0, 0, 0};
+    for (int32_t j = 0; j < n; ++j) cnt[types[r * n + j]]++;
+    cost[r] = s * (costs[0] * (double)cnt[O_TO] + costs[1] * (double)cnt[O_TE] + costs[2] * (double)cnt[O_GO] +
+                   costs[3] * (double)cnt[O_GE]);
+  }
+  return 0;
 }

@@ -103,6 +103,13 @@ def load(path: str = LIB_PATH):
                                ctypes.c_int),
             "famsa_tree_from_edges": ([ctypes.c_int32, ctypes.c_int64] + [_P] * 11 + [ctypes.c_int, _P],
                                       ctypes.c_int),
+            "famsa_progressive_schedule": ([ctypes.c_int32] + [_P] * 7 + [ctypes.c_int, _P], ctypes.c_int),
+            "famsa_gap_types": ([_P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
+            "famsa_gap_scale": ([ctypes.c_int64, ctypes.c_double, ctypes.c_double], ctypes.c_double),
+            "famsa_gap_cost": ([_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_double,
+                                ctypes.c_double, _P, _P], ctypes.c_int),
+            "famsa_gap_insert": ([_P, _P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P],
+                                 ctypes.c_int),
             "famsa_debug_set_serial": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_update_threads": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_sub_kcycles": ([_P, _P], ctypes.c_int),
@@ -380,6 +387,83 @@ def famsa_tree_from_edges(k: int, edges: dict, device: bool = False, stream=None
 
 
 tree_from_edges = famsa_tree_from_edges
+
+
+def famsa_progressive_schedule(tree: dict, device: bool = False, stream=None) -> dict:
+    """The merge list as the progressive stage's schedule: level, order (by level,
+    index), level_start (n_levels + 1 offsets into order) and kind per merge."""
+    merges, sizes = tree["merges"], tree["sizes"]
+    n = len(sizes)
+    k = n + 1
+    _require(merges, np.int32, "merges", count=2 * n)
+    _require(sizes, np.int32, "sizes")
+    out = {"level": _empty(n, np.int32, device), "order": _empty(n, np.int32, device),
+           "level_start": _empty(k, np.int32, device), "kind": _empty(n, np.int32, device)}
+    top = ctypes.c_int32()
+    _check(load().famsa_progressive_schedule(k, _ptr(merges)[0], _ptr(sizes)[0], _ptr(out["level"])[0],
+                                             _ptr(out["order"])[0], _ptr(out["level_start"])[0],
+                                             _ptr(out["kind"])[0], ctypes.byref(top), int(device),
+                                             _stream_ptr(stream)), "famsa_progressive_schedule")
+    out["level_start"] = out["level_start"][:top.value + 1]
+    out["n_levels"] = top.value
+    return out
+
+
+progressive_schedule = famsa_progressive_schedule
+
+
+GAP = 255  # FAMSA_GAP: a gap in alignment rows
+
+
+def famsa_gap_types(aln, stream=None):
+    """Gap types of every cell of an m x n uint8 alignment on the device (torch)."""
+    import torch
+    _require(aln, np.uint8, "aln")
+    m, n = aln.shape
+    out = torch.empty((m, n), dtype=torch.uint8, device=aln.device)
+    _check(load().famsa_gap_types(aln.data_ptr(), m, n, out.data_ptr(), _stream_ptr(stream)),
+           "famsa_gap_types")
+    return out
+
+
+def famsa_gap_scale(k: int, g_l: float = 45.0, g_d: float = 7.0) -> float:
+    """g_scale = 1 + log(k / g_l) / g_d."""
+    return float(load().famsa_gap_scale(k, g_l, g_d))
+
+
+def famsa_gap_cost(types, k: int, costs, g_l: float = 45.0, g_d: float = 7.0, stream=None):
+    """Per row: g_scale(k) x sum of gap counts x costs (T_o, T_e, G_o, G_e); device in, device out."""
+    import torch
+    _require(types, np.uint8, "types")
+    m, n = types.shape
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    if c.shape != (4,):
+        raise ValueError("costs must hold T_o, T_e, G_o, G_e")
+    out = torch.empty(m, dtype=torch.float64, device=types.device)
+    _check(load().famsa_gap_cost(types.data_ptr(), m, n, k, c.ctypes.data, g_l, g_d, out.data_ptr(),
+                                 _stream_ptr(stream)), "famsa_gap_cost")
+    return out
+
+
+def famsa_gap_insert(aln, types, positions, stream=None):
+    """Insert gap columns before original columns positions (ascending) into every
+    row, types corrected by S1..S6: (aln_out, types_out) on the device."""
+    import torch
+    _require(aln, np.uint8, "aln")
+    _require(types, np.uint8, "types", count=aln.numel())
+    m, n = aln.shape
+    p = np.ascontiguousarray(positions, dtype=np.int32)
+    ao = torch.empty((m, n + len(p)), dtype=torch.uint8, device=aln.device)
+    to = torch.empty((m, n + len(p)), dtype=torch.uint8, device=aln.device)
+    _check(load().famsa_gap_insert(aln.data_ptr(), types.data_ptr(), m, n, p.ctypes.data, len(p),
+                                   ao.data_ptr(), to.data_ptr(), _stream_ptr(stream)), "famsa_gap_insert")
+    return ao, to
+
+
+gap_types = famsa_gap_types
+gap_scale = famsa_gap_scale
+gap_cost = famsa_gap_cost
+gap_insert = famsa_gap_insert
 
 
 class Batch:
