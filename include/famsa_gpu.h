@@ -168,6 +168,26 @@ int famsa_lcs_query(const famsa_family *f, const uint8_t *q, const int64_t *q_of
                     void *cuda_stream);
 
 /*
+ * famsa_upgma_tree -- UPGMA, the guide tree the paper names beside single
+ * linkage and sets against it for memory ("Determination of the guide
+ * tree": it needs the whole O(k^2) similarity matrix), over the family's
+ * distances d = indel^2 / LCS as doubles (+inf for LCS = 0).  Each step
+ * joins the live clusters in slots a < b with the smallest (d, a, b) and
+ * sets d(a, c) = (n_a * d(a, c) + n_b * d(b, c)) / (n_a + n_b), each
+ * operation rounded on its own (no fused multiply-add).
+ *   merges (2(k-1)): merge t joins cluster ids (smaller, larger), ids < k
+ *     the caller's sequences, k + t' the cluster of merge t'.
+ *   heights (k-1 doubles): d(a, b) at merge t.  sizes (k-1): the new
+ *     cluster's size.
+ * On the device iff on_device != 0; the call waits for its stream.  It holds
+ * the k x k matrix of doubles and the LCS triangle on the device (k = 20,000:
+ * 4.0 GB).
+ * Errors: EINVAL (NULL), ERANGE (k^2 above 2^34), ENOMEM, ECUDA.
+ */
+int famsa_upgma_tree(const famsa_family *f, int32_t *merges, double *heights, int32_t *sizes, int on_device,
+                     void *cuda_stream);
+
+/*
  * famsa_progressive_schedule -- the merge list in the form the progressive
  * stage consumes ("Progressive construction of the alignment": O(k) profile
  * alignments in guide-tree order, spread over threads; at least half align a

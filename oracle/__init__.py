@@ -30,6 +30,8 @@ Functions and the paper passages they follow (FAMSA, Methods):
 * :func:`gap_types`, :func:`gap_insert`, :func:`gap_scale`, :func:`gap_cost`
   -- the four gap types, gap-column insertion with the six corrections, and
   the set-size gap-cost scaling ("Gap types and costs determination").
+* :func:`distance_matrix`, :func:`upgma` -- UPGMA, the O(k^2)-memory guide
+  tree the paper names beside single linkage, over indel^2 / LCS as doubles.
 * :func:`schedule` -- the merge list as the progressive stage's schedule
   (levels of independent merges, their order, and which merges align a
   single sequence) ("Progressive construction of the alignment").
@@ -64,7 +66,8 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
             tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-            cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC,
+                   "-lm"]
             try:
                 subprocess.check_call(cmd)
             except subprocess.CalledProcessError:
@@ -94,6 +97,8 @@ def _load():
             "oracle_slink_edges": ([i32, i64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
             "oracle_schedule": ([i32, _P, _P, _P, _P, _P, _P], i32),
             "oracle_gap_types": ([_P, i64, i32, _P], ctypes.c_int),
+            "oracle_distance_matrix": ([_P, _P, i32, _P, ctypes.c_int], ctypes.c_int),
+            "oracle_upgma": ([i32, _P, _P, _P, _P], ctypes.c_int),
             "oracle_gap_insert": ([_P, _P, i64, i32, _P, i32, _P, _P], ctypes.c_int),
             "oracle_gap_scale": ([i64, ctypes.c_double, ctypes.c_double], ctypes.c_double),
             "oracle_gap_cost": ([_P, i64, i32, i64, _P, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
@@ -439,3 +444,25 @@ def gap_cost(types, k: int, costs, g_l: float = 45.0, g_d: float = 7.0):
     _check(_load().oracle_gap_cost(_ptr(t), t.shape[0], t.shape[1], k, _ptr(c), g_l, g_d, _ptr(out)),
            "oracle_gap_cost")
     return out
+
+
+# --------------------------------------------------------------------- UPGMA
+def distance_matrix(residues, offsets, nthreads: int = 0) -> np.ndarray:
+    """k x k doubles indel^2 / LCS (+inf for LCS 0, 0 on the diagonal)."""
+    res, off, k = _prep(residues, offsets)
+    D = np.empty((k, k), np.float64)
+    _check(_load().oracle_distance_matrix(_ptr(res), _ptr(off), k, _ptr(D), nthreads),
+           "oracle_distance_matrix")
+    return D
+
+
+def upgma(D):
+    """Plain UPGMA over a distance matrix: dict of merges (k-1, 2), heights, sizes."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    k = D.shape[0]
+    m = max(k - 1, 0)
+    mg = np.empty((max(m, 1), 2), np.int32)
+    h = np.empty(max(m, 1), np.float64)
+    sz = np.empty(max(m, 1), np.int32)
+    _check(_load().oracle_upgma(k, _ptr(D), _ptr(mg), _ptr(h), _ptr(sz)), "oracle_upgma")
+    return {"merges": mg[:m], "heights": h[:m], "sizes": sz[:m]}

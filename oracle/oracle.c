@@ -955,3 +955,80 @@ int oracle_gap_cost(const uint8_t *types, int64_t m, int32_t n, int64_t k, const
   }
   return 0;
 }
+
+/* ------------------------------------------------------------ UPGMA */
+/*
+ * The alternative guide tree the paper names beside single linkage
+ * ("Determination of the guide tree": UPGMA needs the whole O(k^2) matrix).
+ * Distances d(i, j) = indel^2 / LCS as doubles (one correctly rounded
+ * division; +inf for LCS = 0).  Plain UPGMA: while more than one cluster is
+ * left, take the pair of clusters in slots a < b with the smallest
+ * (d, a, b), record it, put the merged cluster in slot a and set, for every
+ * other live slot c,
+ *     d(a, c) = (n_a * d(a, c) + n_b * d(b, c)) / (n_a + n_b)
+ * in exactly that order of operations (no fused multiply-add).  Merge t joins
+ * the clusters of ids (smaller, larger), ids k + t' for earlier merges,
+ * at height d(a, b), making a cluster of sizes[t] sequences.
+ */
+int oracle_distance_matrix(const uint8_t *res, const int64_t *off, int32_t k, double *D, int nthreads) {
+  if (k < 1) return -1;
+  int32_t *tri = (int32_t *)malloc(sizeof(int32_t) * (size_t)((int64_t)k * (k - 1) / 2 + 1));
+  if (!tri) return -2;
+  int rc = oracle_lcs_allpairs(res, off, k, tri, nthreads);
+  if (rc == 0) {
+    for (int32_t i = 0; i < k; ++i) {
+      D[(size_t)i * k + i] = 0.0;
+      for (int32_t j = i + 1; j < k; ++j) {
+        int32_t L = tri[tri_index(i, j, k)];
+        int64_t li = off[i + 1] - off[i], lj = off[j + 1] - off[j];
+        int64_t indel = li + lj - 2 * (int64_t)L;
+        double d = L == 0 ? INFINITY : (double)(indel * indel) / (double)L;
+        D[(size_t)i * k + j] = d;
+        D[(size_t)j * k + i] = d;
+      }
+    }
+  }
+  free(tri);
+  return rc;
+}
+
+int oracle_upgma(int32_t k, const double *D0, int32_t *merges, double *heights, int32_t *sizes) {
+  if (k < 1) return -1;
+  double *D = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  int32_t *id = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t *n = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  char *alive = (char *)malloc((size_t)k);
+  if (!D || !id || !n || !alive) { free(D); free(id); free(n); free(alive); return -2; }
+  memcpy(D, D0, sizeof(double) * (size_t)k * (size_t)k);
+  for (int32_t i = 0; i < k; ++i) { id[i] = i; n[i] = 1; alive[i] = 1; }
+  for (int32_t t = 0; t + 1 < k; ++t) {
+    int32_t ba = -1, bb = -1;
+    double best = 0.0;
+    for (int32_t a = 0; a < k; ++a) {
+      if (!alive[a]) continue;
+      for (int32_t b = a + 1; b < k; ++b) {
+        if (!alive[b]) continue;
+        double d = D[(size_t)a * k + b];
+        if (ba < 0 || d < best) { best = d; ba = a; bb = b; }
+      }
+    }
+    merges[2 * t] = id[ba] < id[bb] ? id[ba] : id[bb];
+    merges[2 * t + 1] = id[ba] < id[bb] ? id[bb] : id[ba];
+    heights[t] = best;
+    double na = (double)n[ba], nb = (double)n[bb], nab = (double)(n[ba] + n[bb]);
+    for (int32_t c = 0; c < k; ++c) {
+      if (!alive[c] || c == ba || c == bb) continue;
+      double x = na * D[(size_t)ba * k + c];
+      double y = nb * D[(size_t)bb * k + c];
+      double v = (x + y) / nab;
+      D[(size_t)ba * k + c] = v;
+      D[(size_t)c * k + ba] = v;
+    }
+    alive[bb] = 0;
+    n[ba] += n[bb];
+    id[ba] = k + t;
+    sizes[t] = n[ba];
+  }
+  free(D); free(id); free(n); free(alive);
+  return 0;
+}

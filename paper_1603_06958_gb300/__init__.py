@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
                                       ctypes.c_int),
             "famsa_progressive_schedule": ([ctypes.c_int32] + [_P] * 7 + [ctypes.c_int, _P], ctypes.c_int),
             "famsa_gap_types": ([_P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
+            "famsa_upgma_tree": ([_P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_gap_scale": ([ctypes.c_int64, ctypes.c_double, ctypes.c_double], ctypes.c_double),
             "famsa_gap_cost": ([_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_double,
                                 ctypes.c_double, _P, _P], ctypes.c_int),
@@ -411,6 +412,24 @@ def famsa_progressive_schedule(tree: dict, device: bool = False, stream=None) ->
 
 progressive_schedule = famsa_progressive_schedule
 
+
+def famsa_upgma_tree(fam: Family, device: bool = False, stream=None) -> dict:
+    """UPGMA over the family's distances indel^2 / LCS: merges (k-1, 2), heights, sizes."""
+    m = max(fam.k - 1, 0)
+    out = {"merges": _empty(2 * m, np.int32, device), "sizes": _empty(m, np.int32, device)}
+    if device:
+        import torch
+        out["heights"] = torch.empty(m, dtype=torch.float64, device="cuda")
+    else:
+        out["heights"] = np.empty(m, np.float64)
+    _check(load().famsa_upgma_tree(fam.handle, _ptr(out["merges"])[0], _ptr(out["heights"])[0],
+                                   _ptr(out["sizes"])[0], int(device), _stream_ptr(stream)),
+           "famsa_upgma_tree")
+    out["merges"] = out["merges"].reshape(m, 2)
+    return out
+
+
+upgma_tree = famsa_upgma_tree
 
 GAP = 255  # FAMSA_GAP: a gap in alignment rows
 
