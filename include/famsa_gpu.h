@@ -48,7 +48,8 @@ typedef enum {
   FAMSA_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed */
   FAMSA_ETIMEOUT = 5, /* a bounded device-side wait gave up */
   FAMSA_EBUSY = 6,    /* the serving queue is full */
-  FAMSA_ELIMIT = 7    /* beyond the fixed limits of famsa_lcs_query_noalloc */
+  FAMSA_ELIMIT = 7,   /* beyond the fixed limits of famsa_lcs_query_noalloc */
+  FAMSA_ECANCELED = 8 /* a serving request cancelled before it started */
 } famsa_status;
 
 /* Opaque handle: a packed family resident on the device.  It owns a device
@@ -446,6 +447,10 @@ void famsa_batch_free(famsa_batch *b);
  * famsa_server_request_info: info[7] int64 = status, kind (0 tree, 1 query),
  *   sequences (k or nq), ns from submission to start (-1 while queued), ns
  *   from submission to completion (-1 before), LCS cells, bytes reserved.
+ * famsa_server_cancel: take a queued request out of the queue; its status
+ *   becomes FAMSA_ECANCELED (queries queued against a cancelled tree request
+ *   then fail with FAMSA_EINVAL).  A running request cannot be stopped (its
+ *   kernels run to the end): FAMSA_EBUSY; unknown or finished: FAMSA_EINVAL.
  * famsa_server_release: forget a request and free a resident family (after
  *   its running queries end).
  * famsa_server_stats: stats[8] int64 = submitted, done, failed, queued,
@@ -468,6 +473,7 @@ int famsa_server_tree_result(famsa_server *s, int64_t request_id, int32_t *pi, u
 int famsa_server_query_result(famsa_server *s, int64_t request_id, int32_t *out);
 int famsa_server_request_info(famsa_server *s, int64_t request_id, int64_t *info);
 int famsa_server_release(famsa_server *s, int64_t request_id);
+int famsa_server_cancel(famsa_server *s, int64_t request_id);
 int famsa_server_stats(famsa_server *s, int64_t *stats);
 void famsa_server_destroy(famsa_server *s);
 

@@ -16,6 +16,15 @@ extern "C" {
  * FAMSA_ENOMEM (n = 0: the next one); n < 0 disables.  Returns FAMSA_OK. */
 int famsa_debug_fail_alloc_after(int n);
 
+/* The family's packed match-bitmask (Peq) tables, copied to the host:
+ * peq (n_words * 64 u32) in the family's (length, index) order -- per word
+ * of a sequence, 32 u32 holding bits 0..31 of the mask of symbols 0..31,
+ * then 32 u32 holding bits 32..63 --, word_off (k + 1 int64: the first word
+ * of each sorted sequence, then the total) and perm (k int32: the caller's
+ * label of each sorted sequence).  Any output may be NULL; n_words receives
+ * the total.  EINVAL for a NULL handle. */
+int famsa_debug_peq(const famsa_family *f, uint32_t *peq, int64_t *word_off, int32_t *perm, int64_t *n_words);
+
 /* The number of device allocations the library has made in this process so
  * far (every one goes through one stream-ordered allocation routine).  Tests
  * use it to check that a call allocates nothing. */

@@ -27,7 +27,7 @@ INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 HEADERS = [os.path.join(INCLUDE, h) for h in ("famsa_gpu.h", "famsa_gpu_debug.h")]
 
 FAMSA_OK, FAMSA_EINVAL, FAMSA_ERANGE, FAMSA_ENOMEM, FAMSA_ECUDA, FAMSA_ETIMEOUT, FAMSA_EBUSY, \
-    FAMSA_ELIMIT = range(8)
+    FAMSA_ELIMIT, FAMSA_ECANCELED = range(9)
 NOALLOC_MAX_QUERIES, NOALLOC_MAX_LEN = 64, 4096
 
 _lib = None
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
             "famsa_server_request_info": ([_P, ctypes.c_int64, _P], ctypes.c_int),
             "famsa_server_release": ([_P, ctypes.c_int64], ctypes.c_int),
             "famsa_server_stats": ([_P, _P], ctypes.c_int),
+            "famsa_server_cancel": ([_P, ctypes.c_int64], ctypes.c_int),
             "famsa_server_destroy": ([_P], None),
             "famsa_free": ([_P], None),
             "famsa_last_stats": ([_P, _P], ctypes.c_int),
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_alloc_count": ([], ctypes.c_int64),
+            "famsa_debug_peq": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "famsa_merge_similarity": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
             "famsa_msf_rows": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, _P],
                                ctypes.c_int),
@@ -621,6 +623,11 @@ class Server:
     def release(self, request_id: int):
         _check(load().famsa_server_release(self.handle, int(request_id)), "famsa_server_release")
 
+    def cancel(self, request_id: int) -> int:
+        """Cancel a queued request: FAMSA_OK; FAMSA_EBUSY while it runs; FAMSA_EINVAL if
+        unknown or finished."""
+        return int(load().famsa_server_cancel(self.handle, int(request_id)))
+
     def stats(self) -> dict:
         a = np.zeros(8, np.int64)
         _check(load().famsa_server_stats(self.handle, a.ctypes.data), "famsa_server_stats")
@@ -726,6 +733,19 @@ def debug_insertion_state(fam: Family) -> dict:
                                                             ("perm", "pi", "lambda_num", "lambda_den")]),
            "famsa_debug_insertion_state")
     return out
+
+
+def debug_peq(fam: Family) -> dict:
+    """The packed Peq tables of a family (host copies): peq (words, 64) uint32,
+    word_off (k + 1), perm (k) in the family's sorted order."""
+    n = ctypes.c_int64()
+    _check(load().famsa_debug_peq(fam.handle, None, None, None, ctypes.byref(n)), "famsa_debug_peq")
+    peq = np.empty((n.value, 64), np.uint32)
+    off = np.empty(fam.k + 1, np.int64)
+    perm = np.empty(fam.k, np.int32)
+    _check(load().famsa_debug_peq(fam.handle, peq.ctypes.data, off.ctypes.data, perm.ctypes.data, None),
+           "famsa_debug_peq")
+    return {"peq": peq, "word_off": off, "perm": perm}
 
 
 def debug_alloc_count() -> int:

@@ -58,6 +58,7 @@ const char *famsa_strerror(int status) {
     case FAMSA_ENOMEM: return "out of memory";
     case FAMSA_ECUDA: return "CUDA error";
     case FAMSA_ETIMEOUT: return "device-side wait timed out";
+    case FAMSA_ECANCELED: return "request cancelled before it started";
     case FAMSA_EBUSY: return "busy (queue full)";
     case FAMSA_ELIMIT: return "beyond the fixed scratch limits of famsa_lcs_query_noalloc (queries, or query length)";
     default: return "unknown status";

@@ -439,3 +439,24 @@ extern "C" int famsa_debug_fail_alloc_after(int n) {
 }
 
 extern "C" int64_t famsa_debug_alloc_count(void) { return famsa::g_alloc_count.load(); }
+
+// The packed match-bitmask tables of a family, for tests: peq (words x 64
+// u32, host) in the family's (length, index) order, the first word of each
+// sequence (k + 1 host int64, the last entry the total), and the caller's
+// label of each sorted sequence (k host int32).  Any output may be NULL; with
+// peq NULL, *n_words still receives the total.
+extern "C" int famsa_debug_peq(const famsa_family *fh, uint32_t *peq, int64_t *word_off, int32_t *perm,
+                               int64_t *n_words) {
+  if (!fh) return FAMSA_EINVAL;
+  const famsa::Family *f = reinterpret_cast<const famsa::Family *>(fh);
+  if (n_words) *n_words = f->peq_words;
+  cudaError_t e = cudaSuccess;
+  if (peq)
+    e = cudaMemcpy(peq, f->d_peq, sizeof(uint32_t) * famsa::kPeqWordU32 * (size_t)f->peq_words,
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word_off)
+    e = cudaMemcpy(word_off, f->d_peq_off, sizeof(int64_t) * ((size_t)f->k + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && perm)
+    e = cudaMemcpy(perm, f->d_perm, sizeof(int32_t) * (size_t)f->k, cudaMemcpyDeviceToHost);
+  return famsa::status_from_cuda(e);
+}

@@ -406,6 +406,27 @@ int famsa_server_request_info(famsa_server *sh, int64_t request_id, int64_t *inf
   return FAMSA_OK;
 }
 
+int famsa_server_cancel(famsa_server *sh, int64_t request_id) {
+  if (!sh) return FAMSA_EINVAL;
+  Server *s = reinterpret_cast<Server *>(sh);
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return FAMSA_EINVAL;
+  Request *r = it->second.get();
+  if (r->status == kRunning) return FAMSA_EBUSY;
+  if (r->status != kQueued) return FAMSA_EINVAL;
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if (*q == r) {
+      s->queue.erase(q);
+      break;
+    }
+  r->status = FAMSA_ECANCELED;
+  r->t_start = r->t_done = now_ns();
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();  // queries waiting on it can now be failed
+  return FAMSA_OK;
+}
+
 int famsa_server_release(famsa_server *sh, int64_t request_id) {
   if (!sh) return FAMSA_EINVAL;
   Server *s = reinterpret_cast<Server *>(sh);

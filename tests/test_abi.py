@@ -45,8 +45,8 @@ def test_probes_live_in_their_own_library(lib):
 
 
 def test_strerror_and_version(lib):
-    for s in range(7):
-        assert len(fg.strerror(s)) > 3
+    for s in range(9):
+        assert len(fg.strerror(s)) > 3 and "unknown" not in fg.strerror(s)
     assert "unknown" in fg.strerror(99)
     assert lib.famsa_version() >= 10000
 
@@ -75,6 +75,7 @@ def test_argument_errors_without_device_work(lib):
     lib.famsa_free(None)
     assert lib.famsa_debug_set_tpp_max_w(99) == fg.FAMSA_EINVAL
     assert lib.famsa_debug_set_cluster(3) == fg.FAMSA_EINVAL
+    assert lib.famsa_server_cancel(None, 0) == fg.FAMSA_EINVAL
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):

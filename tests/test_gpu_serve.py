@@ -115,3 +115,35 @@ def test_failures_stay_per_request(fg):
         assert srv.stats()["failed"] == 2
     finally:
         srv.close()
+
+
+def test_cancel_queued_requests(fg):
+    # one slot: a large tree request runs while the others wait in the queue
+    import time
+    srv = fg.Server(64 << 30, 1)
+    try:
+        big_r, big_o = synth.plain20k(5, k=30000)
+        b_r, b_o = make(FAMS[0])
+        c_r, c_o = make(FAMS[1])
+        a = srv.submit_tree(big_r, big_o)
+        b = srv.submit_tree(b_r, b_o, keep=True)
+        c = srv.submit_tree(c_r, c_o)
+        q, qo = synth.family(5, 51, root_len=60)
+        d = srv.submit_query(b, q, qo)
+        assert srv.cancel(b) == fg.FAMSA_OK          # queued: taken out
+        assert srv.wait(b) == fg.FAMSA_ECANCELED
+        assert srv.cancel(b) == fg.FAMSA_EINVAL       # no longer queued
+        t0 = time.time()
+        while srv.info(a)["status"] == -1 and time.time() - t0 < 30:
+            time.sleep(0.001)
+        if srv.info(a)["status"] == -2:               # running: it cannot be stopped
+            assert srv.cancel(a) == fg.FAMSA_EBUSY
+        assert srv.wait(d) == fg.FAMSA_EINVAL         # its family was cancelled
+        assert srv.wait(c) == fg.FAMSA_OK
+        same_tree(srv.tree_result(c), oracle.tree(c_r, c_o), "after cancel")
+        assert srv.wait(a) == fg.FAMSA_OK
+        assert srv.cancel(a) == fg.FAMSA_EINVAL and srv.cancel(12345) == fg.FAMSA_EINVAL
+        with pytest.raises(fg.FamsaError):
+            srv.tree_result(b)
+    finally:
+        srv.close()
