@@ -88,6 +88,12 @@ int famsa_debug_sub_kcycles(const famsa_family *f, int64_t *out16);
 int famsa_debug_set_tpp_rows(int w, int r);
 int famsa_debug_tpp_rows(int w);
 
+/* on != 0 (default): rows of 24 to 28 64-bit words (one per tile) run the
+ * thread-per-pair step in parts of up to 8 words with the carry passed in a
+ * register; 0: the whole step as one block.  Results are identical.
+ * Returns FAMSA_OK. */
+int famsa_debug_set_tpp_parts(int on);
+
 /* Batch autotuner on (1, default) or off (0; also forgets the widths tuned
  * so far, but keeps their choices until famsa_debug_set_tpp_rows resets them). */
 int famsa_debug_set_autotune(int on);

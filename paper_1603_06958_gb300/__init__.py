@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_alloc_count": ([], ctypes.c_int64),
+            "famsa_debug_set_tpp_parts": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_peq": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "famsa_merge_similarity": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
             "famsa_msf_rows": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, _P],
@@ -746,6 +747,11 @@ def debug_peq(fam: Family) -> dict:
     _check(load().famsa_debug_peq(fam.handle, peq.ctypes.data, off.ctypes.data, perm.ctypes.data, None),
            "famsa_debug_peq")
     return {"peq": peq, "word_off": off, "perm": perm}
+
+
+def debug_set_tpp_parts(on: bool):
+    """Wide thread-per-pair rows in parts of 8 words (default on) or as one step."""
+    _check(load().famsa_debug_set_tpp_parts(int(on)), "famsa_debug_set_tpp_parts")
 
 
 def debug_alloc_count() -> int:

@@ -32,6 +32,10 @@ void set_tpp_rows(int W, int R) {
   if (W >= 1 && W <= kTppMaxW && (R == 0 || tpp_rows_allowed(W, R))) g_tpp_rows[W].store(R);
 }
 
+// Rows of 24..28 words take the step in parts (tpp_use_parts); tests and timing turn it off.
+static std::atomic<int> g_tpp_parts{1};
+bool tpp_parts_enabled() { return g_tpp_parts.load() != 0; }
+
 // Rows wider than this use warp-per-pair (tests lower it to exercise that path).
 static std::atomic<int> g_tpp_max_w{kTppMaxW};
 
@@ -104,6 +108,11 @@ cudaError_t launch_lcs(const LcsBatch &b, cudaStream_t st, int64_t *launches) {
 extern "C" int famsa_debug_set_tpp_max_w(int w) {
   if (w < 0 || w > famsa::kTppMaxW) return FAMSA_EINVAL;
   famsa::g_tpp_max_w.store(w);
+  return FAMSA_OK;
+}
+
+extern "C" int famsa_debug_set_tpp_parts(int on) {
+  famsa::g_tpp_parts.store(on ? 1 : 0);
   return FAMSA_OK;
 }
 

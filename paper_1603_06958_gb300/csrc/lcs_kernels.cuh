@@ -93,13 +93,39 @@ __device__ __forceinline__ void emit_lcs(const KParams &p, int32_t e, int32_t ri
 }
 
 // ------------------------------------------------------------ thread per pair
+// Rows of 24..28 words (one row per tile) run the step in parts of up to 8
+// words with the carry passed between parts in a register, and the register
+// allocator is held to 6 CTAs per SM: only one part's Peq words need to be
+// live at a time, so the kernel keeps twice the resident warps of the
+// one-block step (76-80 registers instead of 136-152).  Measured per width on
+// uniform families: 4-10 % faster at W = 24..28; at 17..20 and 29..32 the
+// one-block step was as fast or faster, so those keep it.
+constexpr bool tpp_use_parts(int W) { return W >= 24 && W <= 28; }
+
+template <int W, int PART>
+__device__ __forceinline__ void lcs_step_parts(uint32_t (&V)[2 * W], const char *base, uint32_t c) {
+  constexpr int w0 = PART * 8;
+  constexpr int N = (W - w0) < 8 ? (W - w0) : 8;
+  constexpr bool last = w0 + N == W;
+  uint32_t P[2 * N];
+#pragma unroll
+  for (int w = 0; w < N; ++w) {
+    P[2 * w] = *reinterpret_cast<const uint32_t *>(base + (w0 + w) * 256);
+    P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + (w0 + w) * 256 + 128);
+  }
+  LcsPart<N, PART == 0 ? 0 : (last ? 2 : 1)>::template run<2 * w0, W>(V, P, c);
+  if constexpr (!last) lcs_step_parts<W, PART + 1>(V, base, c);
+}
+
 // blockIdx.x: tile of R consecutive row entries; blockIdx.y: 128 consecutive
 // sorted columns (4 groups of 32).  Each thread owns one column and runs the
 // recurrence for all R rows of the tile at once (R independent carry chains).
 // With a work list (batched families), work item blockIdx.x names the tile
 // (at most R rows of one family) and its first column group instead.
-template <int W, int R>
-__global__ void __launch_bounds__(kTppThreads) k_lcs_tpp(KParams p) {
+constexpr int tpp_min_ctas(bool parts) { return parts ? 6 : 1; }
+
+template <int W, int R, bool PARTS = false>
+__global__ void __launch_bounds__(kTppThreads, tpp_min_ctas(PARTS)) k_lcs_tpp(KParams p) {
   extern __shared__ __align__(16) uint32_t sPeq[];  // R * W * 64 u32
   int32_t tile_e, tile_end, gbase;
   if (p.items) {
@@ -153,13 +179,17 @@ __global__ void __launch_bounds__(kTppThreads) k_lcs_tpp(KParams p) {
         const char *base = sbase + off;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          uint32_t P[2 * W];
+          if constexpr (PARTS) {
+            lcs_step_parts<W, 0>(V[r], base + r * W * 256, 0u);
+          } else {
+            uint32_t P[2 * W];
 #pragma unroll
-          for (int w = 0; w < W; ++w) {
-            P[2 * w] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256);
-            P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256 + 128);
+            for (int w = 0; w < W; ++w) {
+              P[2 * w] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256);
+              P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256 + 128);
+            }
+            lcs_step<W>(V[r], P);
           }
-          lcs_step<W>(V[r], P);
         }
       }
     }
@@ -255,6 +285,9 @@ __global__ void __launch_bounds__(kWppThreads) k_lcs_wpp(KParams p) {
     if (lane == 0) emit_lcs(p, e, rid, t, L);
   }
 }
+
+// whether rows of 24..28 words take the step in parts (lcs.cu; on by default)
+bool tpp_parts_enabled();
 
 // per-width launchers (defined in the lcs_tpp_*.cu / lcs_wpp.cu units)
 // thread-per-pair launch with R rows per tile (tpp_rows_allowed(W, R))

@@ -5,6 +5,10 @@ tie-heavy small alphabets, duplicates, long sequences (warp-per-pair LCS),
 several row-update cluster sizes and a family too large for one cluster's
 shared memory (global-memory row update), and on repeated graph launches.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -128,11 +132,24 @@ def test_batch_argument_errors(fg):
         fg.batch_pack(bad, o, np.array([0, 5, 10]))       # residue code out of range
 
 
+def _digest(t):
+    h1 = hashlib.sha256()
+    for a, dt in ((t["pi"], "<i4"), (t["lambda_num"], "<u8"), (t["lambda_den"], "<u4")):
+        h1.update(np.ascontiguousarray(a).astype(dt).tobytes())
+    h2 = hashlib.sha256()
+    for a, dt in ((t["merges"], "<i4"), (t["h_num"], "<u8"), (t["h_den"], "<u4"),
+                  (t["sizes"], "<i4")):
+        h2.update(np.ascontiguousarray(a).astype(dt).tobytes())
+    return h1.hexdigest(), h2.hexdigest()
+
+
 def test_batch512_full_size_sampled(fg):
-    # the 512-family batch the bench times, through the same graph: the
-    # families the oracle finishes quickly (all pairs up to 3e9 cells) equal
-    # its trees exactly, a spread of others equal the single-family call, and
-    # every family satisfies the tree invariants
+    # the 512-family batch the bench times, through the same graph: every
+    # family with k <= 500 and 16 seeded others equal the oracle's trees
+    # (digests stored by tests/golden/make_batch_golden.py), the families the
+    # oracle finishes quickly equal its trees computed here, a spread of
+    # others equal the single-family call, and every family satisfies the
+    # tree invariants
     import torch
     fams = synth.batch512(1)
     res, off, fo = concat(fams)
@@ -150,6 +167,12 @@ def test_batch512_full_size_sampled(fg):
     for f in (3, 97, 200, 311, 448, 511):
         r, o = fams[f]
         assert_same(fg.batch_family_tree(out, b, f), alone(fg, r, o), ("alone", f))
+    gold_path = os.path.join(os.path.dirname(__file__), "golden", "oracle_trees.json")
+    gold = json.load(open(gold_path)).get("batch512_seed1", {}).get("families", {})
+    assert len(gold) >= 200
+    for f, want in gold.items():
+        t = {n: np.asarray(v) for n, v in fg.batch_family_tree(out, b, int(f)).items()}
+        assert _digest(t) == (want["pi_lambda_sha256"], want["merges_sha256"]), f
     for f in range(len(fams)):
         t = fg.batch_family_tree(out, b, f)
         k = len(fams[f][1]) - 1

@@ -199,3 +199,26 @@ def test_plain20k_sampled_pairs(fg):
     sample = got[torch.from_numpy(idx).cuda()].cpu().numpy()
     want = oracle.lcs_pairs(res, off, a, b)
     assert np.array_equal(sample, want)
+
+
+@pytest.mark.parametrize("parts", [1, 0])
+def test_wide_rows_in_parts(fg, parts):
+    # rows of 23..29 words: 24..28 take the step in parts with the carry in a
+    # register (unless switched off); both forms equal the oracle
+    rng = np.random.default_rng(77)
+    base = rng.integers(0, 20, 1900).astype(np.uint8)
+    seqs = []
+    for n in range(1450, 1880, 24):
+        s = base[:n].copy()
+        flip = rng.random(n) < 0.15
+        s[flip] = rng.integers(0, 20, int(flip.sum()))
+        seqs.append(s)
+    res, off = family_from(seqs)
+    fg.debug_set_tpp_parts(parts)
+    try:
+        fam = fg.pack_peq(res, off)
+        got = np.asarray(fg.lcs_allpairs(fam))
+        fam.free()
+    finally:
+        fg.debug_set_tpp_parts(1)
+    assert np.array_equal(got, oracle.lcs_allpairs(res, off))
