@@ -806,6 +806,43 @@ def run_int_peaks():
     return 0
 
 
+def run_lcs_widths():
+    """LCS rate per row width on families of one length: thread-per-pair (the
+    step whole, and in parts where that path exists) against warp-per-pair,
+    as fractions of the ALU-pipe peak, from the library's own LCS timers."""
+    import torch
+    import paper_1603_06958_gb300 as fg
+    import synth
+    fg.load()
+    torch.cuda.init()
+    peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9
+    out = []
+    for W in (4, 8, 12, 17, 20, 24, 26, 28, 30, 32, 40, 55):
+        L = 64 * W - 20
+        k = max(1500, int(120000 / W))
+        res, off = synth.family(k, 300 + W, root_len=L, clip_lo=L, clip_hi=L, indel_rate=0.0)
+        fam = fg.pack_peq(res, off)
+        row = {"W": W, "len": L, "k": k}
+        modes = [("wpp", 0, 1)]
+        if W <= 32:
+            modes = [("tpp_whole", 32, 0), ("tpp_parts", 32, 1)] + modes
+        for name, tmax, parts in modes:
+            fg.debug_set_tpp_max_w(tmax)
+            fg.debug_set_tpp_parts(parts)
+            best = None
+            for _ in range(3):
+                fg.slink_tree(fam)
+                st = fam.stats()
+                best = st["lcs_ns"] if best is None else min(best, st["lcs_ns"])
+            row[name] = round(OPS_PER_WORD_STEP * st["word_steps"] / (best * 1e-9) / peak, 4)
+        fg.debug_set_tpp_max_w(32)
+        fg.debug_set_tpp_parts(1)
+        fam.free()
+        out.append(row)
+    print(json.dumps({"lcs_widths": out}), flush=True)
+    return 0
+
+
 def run_cluster_probe():
     """SM clocks of the row update's building blocks on 1- and 16-CTA clusters."""
     import paper_1603_06958_gb300 as fg
@@ -848,6 +885,8 @@ def main():
                     help="batch512: skip timing the one-family-at-a-time comparator")
     ap.add_argument("--cluster-probe", action="store_true",
                     help="time the row update's building blocks (scans, barriers, DSMEM) and exit")
+    ap.add_argument("--lcs-widths", action="store_true",
+                    help="LCS rate per row width: thread-per-pair against warp-per-pair")
     ap.add_argument("--int-peaks", action="store_true",
                     help="measure the integer pipe widths used by the roofline, then exit")
     args = ap.parse_args()
@@ -860,6 +899,8 @@ def main():
         return run_int_peaks()
     if args.cluster_probe:
         return run_cluster_probe()
+    if args.lcs_widths:
+        return run_lcs_widths()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:
