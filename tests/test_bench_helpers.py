@@ -39,7 +39,11 @@ def test_traffic_record_is_current_and_checked_against_sources(tmp_path, monkeyp
     rec = bench.recorded_traffic()
     assert rec is not None, "profiles/lcs_traffic.json no longer matches the LCS sources"
     assert rec["launches"] == len(rec["per_launch"]) and rec["passes"] == 1
-    per = sum(x["dram_read"] + x["dram_write"] for x in rec["per_launch"]) / rec["launches"]
+    # the captured launches' DRAM bytes per ns, times the step's mean LCS launch time
+    got = sum(x["dram_read"] + x["dram_write"] for x in rec["per_launch"])
+    ns = sum(x["ns"] for x in rec["per_launch"])
+    assert got == rec["dram_bytes_captured"] and ns == rec["ns_captured"]
+    per = got / ns * rec["mean_lcs_launch_ns"]
     assert abs(per - rec["dram_bytes_per_launch"]) < 1
     # a copy of the tree with one source changed: the record no longer applies
     for f in rec["sources"] + ["profiles/lcs_traffic.json"]:
