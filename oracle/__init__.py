@@ -30,8 +30,9 @@ Functions and the paper passages they follow (FAMSA, Methods):
 * :func:`gap_types`, :func:`gap_insert`, :func:`gap_scale`, :func:`gap_cost`
   -- the four gap types, gap-column insertion with the six corrections, and
   the set-size gap-cost scaling ("Gap types and costs determination").
-* :func:`distance_matrix`, :func:`upgma` -- UPGMA, the O(k^2)-memory guide
-  tree the paper names beside single linkage, over indel^2 / LCS as doubles.
+* :func:`distance_matrix`, :func:`upgma`, :func:`nj` -- UPGMA and neighbour
+  joining, the O(k^2)-memory guide trees the paper names beside single
+  linkage, over indel^2 / LCS as doubles.
 * :func:`schedule` -- the merge list as the progressive stage's schedule
   (levels of independent merges, their order, and which merges align a
   single sequence) ("Progressive construction of the alignment").
@@ -99,6 +100,7 @@ def _load():
             "oracle_gap_types": ([_P, i64, i32, _P], ctypes.c_int),
             "oracle_distance_matrix": ([_P, _P, i32, _P, ctypes.c_int], ctypes.c_int),
             "oracle_upgma": ([i32, _P, _P, _P, _P], ctypes.c_int),
+            "oracle_nj": ([i32, _P, _P, _P, _P], ctypes.c_int),
             "oracle_gap_insert": ([_P, _P, i64, i32, _P, i32, _P, _P], ctypes.c_int),
             "oracle_gap_scale": ([i64, ctypes.c_double, ctypes.c_double], ctypes.c_double),
             "oracle_gap_cost": ([_P, i64, i32, i64, _P, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
@@ -466,3 +468,17 @@ def upgma(D):
     sz = np.empty(max(m, 1), np.int32)
     _check(_load().oracle_upgma(k, _ptr(D), _ptr(mg), _ptr(h), _ptr(sz)), "oracle_upgma")
     return {"merges": mg[:m], "heights": h[:m], "sizes": sz[:m]}
+
+
+def nj(D):
+    """Plain neighbour joining over a distance matrix: dict of merges (k-1, 2),
+    lengths (k-1, 2) (the branch to each id of the merge), sizes.  Raises
+    RuntimeError (code -3) for an infinite distance."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    k = D.shape[0]
+    m = max(k - 1, 0)
+    mg = np.empty((max(m, 1), 2), np.int32)
+    ln = np.empty((max(m, 1), 2), np.float64)
+    sz = np.empty(max(m, 1), np.int32)
+    _check(_load().oracle_nj(k, _ptr(D), _ptr(mg), _ptr(ln), _ptr(sz)), "oracle_nj")
+    return {"merges": mg[:m], "lengths": ln[:m], "sizes": sz[:m]}
