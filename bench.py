@@ -806,10 +806,10 @@ def run_int_peaks():
     return 0
 
 
-def run_lcs_widths():
-    """LCS rate per row width on families of one length: thread-per-pair (the
-    step whole, and in parts where that path exists) against warp-per-pair,
-    as fractions of the ALU-pipe peak, from the library's own LCS timers."""
+def run_lcs_widths(widths=None, modes=None, reps=3):
+    """LCS rate per row width on families of one length: thread-per-pair, the
+    sliced kernel and warp-per-pair, as fractions of the ALU-pipe peak, from
+    the library's own LCS timers."""
     import torch
     import paper_1603_06958_gb300 as fg
     import synth
@@ -817,28 +817,30 @@ def run_lcs_widths():
     torch.cuda.init()
     peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9
     out = []
-    for W in (4, 8, 12, 17, 20, 24, 26, 28, 30, 32, 40, 55):
+    # (name, thread-per-pair limit, slice minimum width, words per slice)
+    modes_all = [("tpp", 32, 0, 0), ("sliced", 32, 1, 16), ("wpp", 0, 0, 0)]
+    for W in widths or (4, 8, 12, 17, 20, 21, 22, 23, 24, 26, 28, 30, 32, 33, 40, 47, 55, 64, 100, 128, 200):
         L = 64 * W - 20
-        k = max(1500, int(120000 / W))
+        k = max(1000 if W > 100 else 1500, int(120000 / W))
         res, off = synth.family(k, 300 + W, root_len=L, clip_lo=L, clip_hi=L, indel_rate=0.0)
         fam = fg.pack_peq(res, off)
         row = {"W": W, "len": L, "k": k}
-        modes = [("wpp", 0, 1)]
-        if W <= 32:
-            modes = [("tpp_whole", 32, 0), ("tpp_parts", 32, 1)] + modes
-        for name, tmax, parts in modes:
+        for name, tmax, smin, words in modes_all:
+            if name == "tpp" and W > 32 or modes and name not in modes:
+                continue
             fg.debug_set_tpp_max_w(tmax)
-            fg.debug_set_tpp_parts(parts)
+            fg.debug_set_slices(smin, words)
             best = None
-            for _ in range(3):
+            for _ in range(reps):
                 fg.slink_tree(fam)
                 st = fam.stats()
                 best = st["lcs_ns"] if best is None else min(best, st["lcs_ns"])
             row[name] = round(OPS_PER_WORD_STEP * st["word_steps"] / (best * 1e-9) / peak, 4)
         fg.debug_set_tpp_max_w(32)
-        fg.debug_set_tpp_parts(1)
+        fg.debug_set_slices(24, 0)
         fam.free()
         out.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
     print(json.dumps({"lcs_widths": out}), flush=True)
     return 0
 
@@ -886,7 +888,12 @@ def main():
     ap.add_argument("--cluster-probe", action="store_true",
                     help="time the row update's building blocks (scans, barriers, DSMEM) and exit")
     ap.add_argument("--lcs-widths", action="store_true",
-                    help="LCS rate per row width: thread-per-pair against warp-per-pair")
+                    help="LCS rate per row width: thread-per-pair, sliced and warp-per-pair kernels")
+    ap.add_argument("--widths", default="",
+                    help="with --lcs-widths: comma-separated row widths in 64-bit words (default: the sweep)")
+    ap.add_argument("--modes", default="",
+                    help="with --lcs-widths: comma-separated kernels among tpp, sliced, wpp (default: all)")
+    ap.add_argument("--reps", type=int, default=3, help="with --lcs-widths: tree calls per kernel")
     ap.add_argument("--int-peaks", action="store_true",
                     help="measure the integer pipe widths used by the roofline, then exit")
     args = ap.parse_args()
@@ -900,7 +907,8 @@ def main():
     if args.cluster_probe:
         return run_cluster_probe()
     if args.lcs_widths:
-        return run_lcs_widths()
+        return run_lcs_widths([int(w) for w in args.widths.split(",") if w] or None,
+                              [m for m in args.modes.split(",") if m] or None, args.reps)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:

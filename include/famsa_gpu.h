@@ -189,6 +189,32 @@ int famsa_upgma_tree(const famsa_family *f, int32_t *merges, double *heights, in
                      void *cuda_stream);
 
 /*
+ * famsa_nj_tree -- neighbour joining, the other guide tree the paper names
+ * beside single linkage ("Determination of the guide tree"), over the same
+ * distances as famsa_upgma_tree.  With r clusters live, R(i) is the sum of
+ * d(i, j) over the live j != i (added in increasing j) and the live slots
+ * a < b with the smallest (Q, a, b), Q = (r - 2) d(a, b) - R(a) - R(b), are
+ * joined with branches delta_a = d(a, b) / 2 + (R(a) - R(b)) / (2 (r - 2))
+ * and delta_b = d(a, b) - delta_a; the new cluster takes slot a with
+ * d(a, c) = (d(a, c) + d(b, c) - d(a, b)) / 2.  The last two clusters are
+ * joined with d(a, b) / 2 on each branch (the root).  Every operation is
+ * rounded on its own, in that order (no fused multiply-add).
+ *   merges (2(k-1)): merge t joins cluster ids (smaller, larger), as
+ *     famsa_upgma_tree.
+ *   lengths (2(k-1) doubles): the branch lengths to merges[2t] and
+ *     merges[2t+1] (they may be negative: neighbour joining does not
+ *     prevent it).  sizes (k-1): the new cluster's size.
+ * On the device iff on_device != 0; the call waits for its stream.  It holds
+ * the k x k matrix of doubles on the device; each step is O(k^2) in FP64, so
+ * the tree is O(k^3) (k = 8,192: about a second).
+ * Errors: EINVAL (NULL), ERANGE (k above 32,768, or a pair with LCS 0: an
+ *   infinite distance, for which neighbour joining is undefined), ENOMEM,
+ *   ECUDA.
+ */
+int famsa_nj_tree(const famsa_family *f, int32_t *merges, double *lengths, int32_t *sizes, int on_device,
+                  void *cuda_stream);
+
+/*
  * famsa_progressive_schedule -- the merge list in the form the progressive
  * stage consumes ("Progressive construction of the alignment": O(k) profile
  * alignments in guide-tree order, spread over threads; at least half align a

@@ -30,11 +30,22 @@ int famsa_debug_peq(const famsa_family *f, uint32_t *peq, int64_t *word_off, int
  * use it to check that a call allocates nothing. */
 int64_t famsa_debug_alloc_count(void);
 
-/* Rows wider than w 64-bit words use the warp-per-pair LCS kernel instead of
- * thread-per-pair (default 32, the thread-per-pair maximum; 0 sends every
- * row to warp-per-pair).  Results are identical either way.  Returns
- * FAMSA_EINVAL for w outside 0..32. */
+/* Rows wider than w 64-bit words do not use the thread-per-pair LCS kernel
+ * (default 32, the thread-per-pair maximum): they take the sliced kernel
+ * where famsa_debug_set_slices covers their width, else warp-per-pair (with
+ * slices off, 0 sends every row to warp-per-pair).  Results are identical
+ * either way.  Returns FAMSA_EINVAL for w outside 0..32. */
 int famsa_debug_set_tpp_max_w(int w);
+
+/* Rows of at least min_w words (64 residues each) run on the sliced kernel:
+ * the row's bit vector split across up to 16 warps of at most `words` words
+ * each (1..16; 0 = 16), the add's carries passed from warp to warp through
+ * shared memory once per 16 column symbols.  min_w = 0 turns it off (rows
+ * then take thread-per-pair up to famsa_debug_set_tpp_max_w, warp-per-pair
+ * beyond); the default is 24.  Rows wider than 256 words always take
+ * warp-per-pair.  Results are identical for every setting.  Returns
+ * FAMSA_EINVAL for a negative min_w or words outside 0..16. */
+int famsa_debug_set_slices(int min_w, int words);
 
 /* Force the number of CTAs in the thread-block cluster that runs the SLINK
  * row update (1, 2, 4, 8 or 16; 0 = automatic, the largest that fits).
@@ -87,12 +98,6 @@ int famsa_debug_sub_kcycles(const famsa_family *f, int64_t *out16);
  * values.  famsa_debug_tpp_rows returns the r in use for w (-1 for a bad w). */
 int famsa_debug_set_tpp_rows(int w, int r);
 int famsa_debug_tpp_rows(int w);
-
-/* on != 0 (default): rows of 24 to 28 64-bit words (one per tile) run the
- * thread-per-pair step in parts of up to 8 words with the carry passed in a
- * register; 0: the whole step as one block.  Results are identical.
- * Returns FAMSA_OK. */
-int famsa_debug_set_tpp_parts(int on);
 
 /* Batch autotuner on (1, default) or off (0; also forgets the widths tuned
  * so far, but keeps their choices until famsa_debug_set_tpp_rows resets them). */

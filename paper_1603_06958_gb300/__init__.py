@@ -99,7 +99,7 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_update_path": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_alloc_count": ([], ctypes.c_int64),
-            "famsa_debug_set_tpp_parts": ([ctypes.c_int], ctypes.c_int),
+            "famsa_debug_set_slices": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "famsa_debug_peq": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "famsa_merge_similarity": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
             "famsa_msf_rows": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, _P],
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
             "famsa_progressive_schedule": ([ctypes.c_int32] + [_P] * 7 + [ctypes.c_int, _P], ctypes.c_int),
             "famsa_gap_types": ([_P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
             "famsa_upgma_tree": ([_P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+            "famsa_nj_tree": ([_P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
             "famsa_gap_scale": ([ctypes.c_int64, ctypes.c_double, ctypes.c_double], ctypes.c_double),
             "famsa_gap_cost": ([_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_double,
                                 ctypes.c_double, _P, _P], ctypes.c_int),
@@ -434,6 +435,27 @@ def famsa_upgma_tree(fam: Family, device: bool = False, stream=None) -> dict:
 
 upgma_tree = famsa_upgma_tree
 
+
+def famsa_nj_tree(fam: Family, device: bool = False, stream=None) -> dict:
+    """Neighbour joining over the family's distances indel^2 / LCS: merges
+    (k-1, 2), lengths (k-1, 2) (the branch to each id of a merge), sizes."""
+    m = max(fam.k - 1, 0)
+    out = {"merges": _empty(2 * m, np.int32, device), "sizes": _empty(m, np.int32, device)}
+    if device:
+        import torch
+        out["lengths"] = torch.empty(2 * m, dtype=torch.float64, device="cuda")
+    else:
+        out["lengths"] = np.empty(2 * m, np.float64)
+    _check(load().famsa_nj_tree(fam.handle, _ptr(out["merges"])[0], _ptr(out["lengths"])[0],
+                                _ptr(out["sizes"])[0], int(device), _stream_ptr(stream)),
+           "famsa_nj_tree")
+    out["merges"] = out["merges"].reshape(m, 2)
+    out["lengths"] = out["lengths"].reshape(m, 2)
+    return out
+
+
+nj_tree = famsa_nj_tree
+
 GAP = 255  # FAMSA_GAP: a gap in alignment rows
 
 
@@ -716,8 +738,15 @@ def debug_fail_alloc_after(n: int):
 
 
 def debug_set_tpp_max_w(w: int):
-    """Rows wider than w words use the warp-per-pair kernel (32 = default)."""
+    """Rows wider than w words leave thread-per-pair (32 = default) for the
+    sliced kernel where it is on for their width, else warp-per-pair."""
     _check(load().famsa_debug_set_tpp_max_w(w), "famsa_debug_set_tpp_max_w")
+
+
+def debug_set_slices(min_w: int, words: int = 0):
+    """Rows of at least min_w words run sliced (0 = off; default 24), slices of
+    at most `words` words (0 = 16)."""
+    _check(load().famsa_debug_set_slices(min_w, words), "famsa_debug_set_slices")
 
 
 def debug_set_update_path(path: int):
@@ -747,11 +776,6 @@ def debug_peq(fam: Family) -> dict:
     _check(load().famsa_debug_peq(fam.handle, peq.ctypes.data, off.ctypes.data, perm.ctypes.data, None),
            "famsa_debug_peq")
     return {"peq": peq, "word_off": off, "perm": perm}
-
-
-def debug_set_tpp_parts(on: bool):
-    """Wide thread-per-pair rows in parts of 8 words (default on) or as one step."""
-    _check(load().famsa_debug_set_tpp_parts(int(on)), "famsa_debug_set_tpp_parts")
 
 
 def debug_alloc_count() -> int:

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libfamsa_gpu.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu", "lcs_tpp_d.cu",
-           "lcs_wpp.cu", "slink.cu", "slink_global.cu", "slink_smem.cu", "slink_msf.cu", "shard.cu", "schedule.cu", "gaps.cu", "upgma.cu", "finalize.cu",
+           "lcs_slice_a.cu", "lcs_slice_b.cu", "lcs_wpp.cu", "slink.cu", "slink_global.cu", "slink_smem.cu", "slink_msf.cu", "shard.cu", "schedule.cu", "gaps.cu", "upgma.cu", "finalize.cu",
            "noalloc.cu", "batch.cu", "server.cu"]
 # microbenchmarks behind the roofline figures: a separate library that only
 # bench.py loads (--int-peaks, --cluster-probe), not part of the product ABI

@@ -334,16 +334,9 @@ static cudaError_t upload_vec(Arena &A, const std::vector<T> &v, T **d, cudaStre
   return cudaMemcpyAsync(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
 }
 
-static int wpp_NW(int W) {
-  int nw = 1;
-  while (32 * nw < W) nw *= 2;
-  return nw;
-}
-
 struct Bucket {
-  bool wpp;
-  int kw;     // W (thread-per-pair) or NW (warp-per-pair)
-  int R = 1;  // rows per tile
+  LcsChoice c;  // the LCS kernel of its rows (lcs_choice of their width)
+  int R = 1;    // rows per tile
   // one descriptor per row tile: (first row entry, rows, first column group,
   // group step); its work items take the column groups gstart + j * gstep
   std::vector<int4> tiles;
@@ -362,7 +355,12 @@ struct RowArrays {
   std::vector<int32_t> len, id;
 };
 
-static void append_rows(const Batch *b, const std::vector<BRow> &rows, size_t count, bool wpp, int R,
+// columns per work item: thread-per-pair 4 groups, sliced 1 group, warp-per-pair kWppCols
+static int item_cols(const LcsChoice &c) {
+  return c.kind == kLcsTpp ? 4 * kGroup : (c.kind == kLcsSlice ? kGroup : kWppCols);
+}
+
+static void append_rows(const Batch *b, const std::vector<BRow> &rows, size_t count, int cols, int R,
                         const std::vector<int64_t> &h_peq_off, const std::vector<int64_t> &rb_off,
                         const std::vector<int64_t> &ld, RowArrays &ra, std::vector<int4> &tiles,
                         std::vector<int32_t> &tile_items) {
@@ -379,12 +377,10 @@ static void append_rows(const Batch *b, const std::vector<BRow> &rows, size_t co
       ra.id.push_back(rid);
       ra.base.push_back(rb_off[f] + (int64_t)(rid - b->S[f] - 1) * ld[f] - b->S[f]);
     }
-    // the tile meets the columns [S[f], rid_last): thread-per-pair items take
-    // 4 column groups (128 columns) each, warp-per-pair items kWppCols columns
+    // the tile meets the columns [S[f], rid_last), `cols` of them per item
     const int32_t rid_last = rows[j - 1].rid;
     const int32_t g0 = (int32_t)(b->S[f] / kGroup);  // S[f] is a multiple of kGroup
     const int32_t span = rid_last - g0 * kGroup;
-    const int32_t cols = wpp ? kWppCols : 4 * kGroup;
     tiles.push_back(make_int4(e0, (int)(j - i), g0, cols / kGroup));
     tile_items.push_back(span > 0 ? (span + cols - 1) / cols : 0);
     i = j;
@@ -452,7 +448,7 @@ static cudaError_t time_rows(const Batch *b, uint16_t *rowbuf, const std::vector
   RowArrays ra;
   std::vector<int4> tiles, items;
   std::vector<int32_t> tile_items;
-  append_rows(b, rows, count, false, R, h_peq_off, rb_off, ld, ra, tiles, tile_items);
+  append_rows(b, rows, count, 4 * kGroup, R, h_peq_off, rb_off, ld, ra, tiles, tile_items);
   expand_on_host(tiles, tile_items, items);
   int64_t *d_peq = nullptr, *d_base = nullptr;
   int32_t *d_len = nullptr, *d_id = nullptr;
@@ -505,31 +501,32 @@ static cudaError_t autotune_rows(Batch *b, uint16_t *rowbuf, const std::vector<B
   for (size_t bk = 0; bk < buckets.size(); ++bk) {
     const Bucket &B = buckets[bk];
     const auto &rows = rows_by_bucket[bk];
-    if (B.wpp || g_tuned[B.kw] || rows.size() < kTuneMinRows) continue;
+    if (B.c.kind != kLcsTpp || g_tuned[B.c.kw] || rows.size() < kTuneMinRows) continue;
     // rows in bucket order until the sample holds kTuneWordSteps (a row of W
     // words takes W word steps per residue of the columns before it)
     size_t count = 0;
     double steps = 0.0;
     while (count < rows.size() && steps < kTuneWordSteps) {
       const BRow &r = rows[count];
-      steps += (double)B.kw * (double)(len_pre[r.rid] - len_pre[b->S[r.f]]);
+      steps += (double)B.c.kw * (double)(len_pre[r.rid] - len_pre[b->S[r.f]]);
       ++count;
     }
-    const int R0 = tpp_default_rows(B.kw);
+    const int W = B.c.kw;
+    const int R0 = tpp_default_rows(W);
     int best_R = R0;
     float best_ms = 0.f;
-    cudaError_t e = time_rows(b, rowbuf, rows, count, B.kw, R0, h_peq_off, rb_off, ld, st, &best_ms);
+    cudaError_t e = time_rows(b, rowbuf, rows, count, W, R0, h_peq_off, rb_off, ld, st, &best_ms);
     if (e != cudaSuccess) return e;
     const float bar = best_ms * (float)kTuneMargin;
     for (int R : {1, 2, 4}) {
-      if (R == R0 || !tpp_rows_allowed(B.kw, R)) continue;
+      if (R == R0 || !tpp_rows_allowed(W, R)) continue;
       float ms = 0.f;
-      e = time_rows(b, rowbuf, rows, count, B.kw, R, h_peq_off, rb_off, ld, st, &ms);
+      e = time_rows(b, rowbuf, rows, count, W, R, h_peq_off, rb_off, ld, st, &ms);
       if (e != cudaSuccess) return e;
       if (ms < bar && ms < best_ms) { best_ms = ms; best_R = R; }
     }
-    set_tpp_rows(B.kw, best_R);
-    g_tuned[B.kw] = true;
+    set_tpp_rows(W, best_R);
+    g_tuned[W] = true;
     b->stats[10] += 1;
   }
   b->stats[11] = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
@@ -556,15 +553,18 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   }
   // row entries, grouped by kernel width; within a width, family by family
   std::vector<Bucket> buckets;
-  std::vector<int> bucket_of(64 + 7, -1);
+  std::vector<int> bucket_of(kMaxLen / 64 + 2, -1);  // per row width
   auto bucket_for = [&](int W) -> int {
-    const bool wpp = W > kTppMaxW;
-    const int key = wpp ? 33 + __builtin_ctz(wpp_NW(W)) : W;
-    if (bucket_of[key] < 0) {
-      bucket_of[key] = (int)buckets.size();
-      buckets.push_back(Bucket{wpp, wpp ? wpp_NW(W) : W, {}});
+    if (bucket_of[W] < 0) {
+      const LcsChoice c = lcs_choice(W);
+      for (size_t i = 0; i < buckets.size() && bucket_of[W] < 0; ++i)
+        if (buckets[i].c == c) bucket_of[W] = (int)i;
+      if (bucket_of[W] < 0) {
+        bucket_of[W] = (int)buckets.size();
+        buckets.push_back(Bucket{c});
+      }
     }
-    return bucket_of[key];
+    return bucket_of[W];
   };
   std::vector<std::vector<int64_t>> e_peq(1), e_base(1);
   std::vector<std::vector<int32_t>> e_len(1), e_id(1);
@@ -598,7 +598,8 @@ static int batch_plan(Batch *b, cudaStream_t st) {
     std::vector<int> order(buckets.size());
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int x, int y) {
-      return buckets[x].wpp != buckets[y].wpp ? buckets[y].wpp : buckets[x].kw < buckets[y].kw;
+      const LcsChoice &a = buckets[x].c, &c = buckets[y].c;
+      return a.kind != c.kind ? a.kind < c.kind : a.kw * a.g < c.kw * c.g;
     });
     std::vector<Bucket> nb;
     std::vector<std::vector<BRow>> nr;
@@ -640,9 +641,9 @@ static int batch_plan(Batch *b, cudaStream_t st) {
   // second pass: row arrays and work items
   for (size_t bk = 0; bk < buckets.size(); ++bk) {
     Bucket &B = buckets[bk];
-    B.R = B.wpp ? 1 : tpp_rows(B.kw);
-    append_rows(b, rows_by_bucket[bk], rows_by_bucket[bk].size(), B.wpp, B.R, h_peq_off, rb_off, ld, ra,
-                B.tiles, B.tile_items);
+    B.R = B.c.kind == kLcsTpp ? tpp_rows(B.c.kw) : 1;
+    append_rows(b, rows_by_bucket[bk], rows_by_bucket[bk].size(), item_cols(B.c), B.R, h_peq_off, rb_off, ld,
+                ra, B.tiles, B.tile_items);
   }
   // item offsets per bucket and per tile (the items themselves are expanded on the device)
   std::vector<int64_t> item_off(buckets.size() + 1, 0);
@@ -841,8 +842,10 @@ static int batch_plan(Batch *b, cudaStream_t st) {
           p.items = d_items + item_off[bk];
           p.e0 = 0;
           p.e1 = (int32_t)ra.id.size();
-          e = buckets[bk].wpp ? launch_wpp(buckets[bk].kw, p, dim3((unsigned)n), b->cap)
-                              : launch_tpp(buckets[bk].kw, buckets[bk].R, p, dim3((unsigned)n), b->cap);
+          const LcsChoice &c = buckets[bk].c;
+          e = c.kind == kLcsTpp ? launch_tpp(c.kw, buckets[bk].R, p, dim3((unsigned)n), b->cap)
+              : c.kind == kLcsSlice ? launch_slice(c.kw, c.g, p, dim3((unsigned)n), b->cap)
+                                    : launch_wpp(c.kw, p, dim3((unsigned)n), b->cap);
           ++launches;
         }
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_stage[g], b->cap);

@@ -11,12 +11,11 @@ is not preserved between separate asm statements, so the whole W-word update
 is emitted as a single asm block per W.  lop3 with LUT 0xF4 computes
 a | (b & ~c) for (a, b, c) = (s, V, P).
 
-For wide vectors the same step is also emitted in parts of up to 8 words
-(LcsPart<N, MODE>::run<OFF, W>: words OFF/2 .. OFF/2 + N of a W-word
-vector): the carry crosses from one part to the next through a register
-(captured with addc.u32 c, 0, 0 and restored with add.cc.u32 t, c, 0xFFFFFFFF), so
-only one part's Peq words need to be live at a time.  MODE 0 is the first
-part (carry out), 1 a middle part (carry in and out), 2 the last (carry in).
+A slice of N words of a vector split across warps (LcsSlice<N>::run) takes
+its carry in from the top bit of a mask register, shifting the mask left
+(add.cc.u32 m, m, m), and appends its carry out at bit 0 of another
+(addc.u32 o, o, o): sixteen steps in a row leave their carries in one
+16-bit field, which the next slice reads back in the same order.
 
 Run: python gen_lcs_step.py > lcs_step.inc   (the build does this when the
 generated file is older than this script).
@@ -52,37 +51,28 @@ def emit(W: int) -> str:
     return "\n".join(lines)
 
 
-PART_MAX = 8
+SLICE_MAX = 16
 
 
-def emit_part(N: int, mode: int) -> str:
+def emit_slice(N: int) -> str:
     n = 2 * N
-    body = ["{", ".reg .b32 u<%d>, s<%d>, t;" % (n, n)]
+    body = ["{", ".reg .b32 u<%d>, s<%d>;" % (n, n)]
     for i in range(n):
-        body.append("and.b32 u%d, %%%d, %%%d;" % (i, i, n + 1 + i))
-    if mode != 0:
-        body.append("add.cc.u32 t, %%%d, 0xFFFFFFFF;" % n)  # CF = carry in
+        body.append("and.b32 u%d, %%%d, %%%d;" % (i, i, n + 2 + i))
+    body.append("add.cc.u32 %%%d, %%%d, %%%d;" % (n, n, n))  # CF = top bit of the carry-in mask
     for i in range(n):
-        if i == 0 and mode == 0:
-            op = "add.cc.u32"
-        elif i == n - 1 and mode == 2:
-            op = "addc.u32"
-        else:
-            op = "addc.cc.u32"
-        body.append("%s s%d, %%%d, u%d;" % (op, i, i, i))
-    if mode != 2:
-        body.append("addc.u32 %%%d, 0, 0;" % n)  # carry out
+        body.append("addc.cc.u32 s%d, %%%d, u%d;" % (i, i, i))
+    body.append("addc.u32 %%%d, %%%d, %%%d;" % (n + 1, n + 1, n + 1))  # carry out into bit 0
     for i in range(n):
-        body.append("lop3.b32 %%%d, s%d, %%%d, %%%d, 0xF4;" % (i, i, i, n + 1 + i))
+        body.append("lop3.b32 %%%d, s%d, %%%d, %%%d, 0xF4;" % (i, i, i, n + 2 + i))
     body.append("}")
     asm = "\\n\\t".join(body)
-    outs = ", ".join(['"+r"(v[OFF + %d])' % i for i in range(n)] + ['"+r"(c)'])
+    outs = ", ".join(['"+r"(v[%d])' % i for i in range(n)] + ['"+r"(cin)', '"+r"(cout)'])
     ins = ", ".join('"r"(p[%d])' % i for i in range(n))
-    return ("template <> struct LcsPart<%d, %d> {\n"
-            "  template <int OFF, int W>\n"
-            "  __device__ __forceinline__ static void run(uint32_t (&v)[2 * W], const uint32_t (&p)[%d], "
-            "uint32_t &c) {\n"
-            '    asm("%s"\n        : %s\n        : %s);\n  }\n};' % (N, mode, n, asm, outs, ins))
+    return ("template <> struct LcsSlice<%d> {\n"
+            "  __device__ __forceinline__ static void run(uint32_t (&v)[%d], const uint32_t (&p)[%d], "
+            "uint32_t &cin, uint32_t &cout) {\n"
+            '    asm("%s"\n        : %s\n        : %s);\n  }\n};' % (N, n, n, asm, outs, ins))
 
 
 def main():
@@ -91,11 +81,10 @@ def main():
            "template <int W> __device__ __forceinline__ void lcs_step(uint32_t (&v)[2 * W], const uint32_t (&p)[2 * W]);"]
     for W in range(1, MAX_W + 1):
         out.append(emit(W))
-    out.append("// parts of up to %d words of a wide vector, the carry passed in c" % PART_MAX)
-    out.append("template <int N, int MODE> struct LcsPart;")
-    for N in range(1, PART_MAX + 1):
-        for mode in (0, 1, 2):
-            out.append(emit_part(N, mode))
+    out.append("// slices of up to %d words, carries in and out through bit masks" % SLICE_MAX)
+    out.append("template <int N> struct LcsSlice;")
+    for N in range(1, SLICE_MAX + 1):
+        out.append(emit_slice(N))
     sys.stdout.write("\n".join(out) + "\n")
 
 

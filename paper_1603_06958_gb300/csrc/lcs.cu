@@ -1,6 +1,7 @@
 // Launch planning for the LCS kernels: split a row list (sorted by width)
-// into segments of one kernel width and launch thread-per-pair or
+// into segments of one kernel choice and launch thread-per-pair, sliced or
 // warp-per-pair kernels over the family's length-sorted column groups.
+#include <algorithm>
 #include <atomic>
 
 #include "lcs_kernels.cuh"
@@ -11,6 +12,14 @@ cudaError_t launch_tpp_a(int W, int R, const KParams &p, dim3 grid, cudaStream_t
 cudaError_t launch_tpp_b(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
 cudaError_t launch_tpp_c(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
 cudaError_t launch_tpp_d(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
+
+cudaError_t launch_slice_a(int WL, int G, const KParams &p, dim3 grid, cudaStream_t st);
+cudaError_t launch_slice_b(int WL, int G, const KParams &p, dim3 grid, cudaStream_t st);
+
+cudaError_t launch_slice(int WL, int G, const KParams &p, dim3 grid, cudaStream_t st) {
+  if (WL < 1 || WL > kSliceWords || G < 1 || G > kSliceMaxG) return cudaErrorInvalidValue;
+  return WL <= 8 ? launch_slice_a(WL, G, p, grid, st) : launch_slice_b(WL, G, p, grid, st);
+}
 
 cudaError_t launch_tpp(int W, int R, const KParams &p, dim3 grid, cudaStream_t st) {
   if (W < 1 || W > kTppMaxW || !tpp_rows_allowed(W, R)) return cudaErrorInvalidValue;
@@ -32,12 +41,14 @@ void set_tpp_rows(int W, int R) {
   if (W >= 1 && W <= kTppMaxW && (R == 0 || tpp_rows_allowed(W, R))) g_tpp_rows[W].store(R);
 }
 
-// Rows of 24..28 words take the step in parts (tpp_use_parts); tests and timing turn it off.
-static std::atomic<int> g_tpp_parts{1};
-bool tpp_parts_enabled() { return g_tpp_parts.load() != 0; }
-
-// Rows wider than this use warp-per-pair (tests lower it to exercise that path).
+// Rows wider than this do not use thread-per-pair (tests lower it to exercise the other kernels).
 static std::atomic<int> g_tpp_max_w{kTppMaxW};
+// Rows of at least this many words use the sliced kernel (0: never), in
+// slices of at most g_slice_words words.  Thread-per-pair keeps a row's whole
+// vector in one thread's registers; from 24 words on that costs it
+// resident warps, and two or more slices of 12..16 words run faster.
+static std::atomic<int> g_slice_min_w{kSliceMinW};
+static std::atomic<int> g_slice_words{kSliceWords};
 
 static int wpp_nw(int W) {
   int nw = 1;
@@ -45,9 +56,23 @@ static int wpp_nw(int W) {
   return nw;
 }
 
+LcsChoice lcs_choice(int W) {
+  const int smin = g_slice_min_w.load(), tmax = g_tpp_max_w.load();
+  const bool slice = smin > 0 && W >= smin && W <= kSliceMaxW;
+  if (W <= tmax && !slice) return LcsChoice{kLcsTpp, W, 1};
+  if (slice) {
+    // a power of two of slices (CTAs of 3, 5, 6, 7 warps measured 15-25 % slower
+    // than 2 or 4), each as even as whole words allow
+    const int wl0 = std::max(g_slice_words.load(), (W + kSliceMaxG - 1) / kSliceMaxG);
+    int g = 1;
+    while (g * wl0 < W) g *= 2;
+    return LcsChoice{kLcsSlice, (W + g - 1) / g, g};
+  }
+  return LcsChoice{kLcsWpp, wpp_nw(W), 1};
+}
+
 cudaError_t launch_lcs(const LcsBatch &b, cudaStream_t st, int64_t *launches) {
   if (b.n_rows <= 0 || b.n_cols <= 0) return cudaSuccess;
-  const int tmax = g_tpp_max_w.load();
   KParams p;
   p.peq = b.peq;
   p.row_peq_off = b.row_peq_off;
@@ -71,29 +96,25 @@ cudaError_t launch_lcs(const LcsBatch &b, cudaStream_t st, int64_t *launches) {
   p.row_base = b.row_base;
   int32_t e0 = 0;
   while (e0 < b.n_rows) {
-    const int w0 = b.h_row_w[e0];
-    const bool wpp = w0 > tmax;
-    const int kw = wpp ? wpp_nw(w0) : w0;
+    const LcsChoice c = lcs_choice(b.h_row_w[e0]);
     int32_t e1 = e0 + 1;
-    while (e1 < b.n_rows) {
-      const int w = b.h_row_w[e1];
-      const bool wp = w > tmax;
-      if (wp != wpp || (wp ? wpp_nw(w) : w) != kw) break;
-      ++e1;
-    }
+    while (e1 < b.n_rows && lcs_choice(b.h_row_w[e1]) == c) ++e1;
     p.e0 = e0;
     p.e1 = e1;
     // columns needed: triangle mode stops at the largest row id of the segment
     int64_t col_bound = b.triangle ? b.h_row_id[e1 - 1] : b.n_cols;
     if (col_bound > 0) {
       cudaError_t err;
-      if (!wpp) {
-        int R = tpp_rows(kw);
+      if (c.kind == kLcsTpp) {
+        int R = tpp_rows(c.kw);
         dim3 grid((unsigned)((e1 - e0 + R - 1) / R), (unsigned)((col_bound + kTppThreads - 1) / kTppThreads));
-        err = launch_tpp(kw, R, p, grid, st);
+        err = launch_tpp(c.kw, R, p, grid, st);
+      } else if (c.kind == kLcsSlice) {
+        dim3 grid((unsigned)(e1 - e0), (unsigned)((col_bound + kGroup - 1) / kGroup));
+        err = launch_slice(c.kw, c.g, p, grid, st);
       } else {
         dim3 grid((unsigned)(e1 - e0), (unsigned)((col_bound + kWppCols - 1) / kWppCols));
-        err = launch_wpp(kw, p, grid, st);
+        err = launch_wpp(c.kw, p, grid, st);
       }
       if (err != cudaSuccess) return err;
       if (launches) ++*launches;
@@ -111,8 +132,10 @@ extern "C" int famsa_debug_set_tpp_max_w(int w) {
   return FAMSA_OK;
 }
 
-extern "C" int famsa_debug_set_tpp_parts(int on) {
-  famsa::g_tpp_parts.store(on ? 1 : 0);
+extern "C" int famsa_debug_set_slices(int min_w, int words) {
+  if (min_w < 0 || words < 0 || words > famsa::kSliceWords) return FAMSA_EINVAL;
+  famsa::g_slice_min_w.store(min_w);
+  famsa::g_slice_words.store(words ? words : famsa::kSliceWords);
   return FAMSA_OK;
 }
 

@@ -93,39 +93,16 @@ __device__ __forceinline__ void emit_lcs(const KParams &p, int32_t e, int32_t ri
 }
 
 // ------------------------------------------------------------ thread per pair
-// Rows of 24..28 words (one row per tile) run the step in parts of up to 8
-// words with the carry passed between parts in a register, and the register
-// allocator is held to 6 CTAs per SM: only one part's Peq words need to be
-// live at a time, so the kernel keeps twice the resident warps of the
-// one-block step (76-80 registers instead of 136-152).  Measured per width on
-// uniform families: 4-10 % faster at W = 24..28; at 17..20 and 29..32 the
-// one-block step was as fast or faster, so those keep it.
-constexpr bool tpp_use_parts(int W) { return W >= 24 && W <= 28; }
-
-template <int W, int PART>
-__device__ __forceinline__ void lcs_step_parts(uint32_t (&V)[2 * W], const char *base, uint32_t c) {
-  constexpr int w0 = PART * 8;
-  constexpr int N = (W - w0) < 8 ? (W - w0) : 8;
-  constexpr bool last = w0 + N == W;
-  uint32_t P[2 * N];
-#pragma unroll
-  for (int w = 0; w < N; ++w) {
-    P[2 * w] = *reinterpret_cast<const uint32_t *>(base + (w0 + w) * 256);
-    P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + (w0 + w) * 256 + 128);
-  }
-  LcsPart<N, PART == 0 ? 0 : (last ? 2 : 1)>::template run<2 * w0, W>(V, P, c);
-  if constexpr (!last) lcs_step_parts<W, PART + 1>(V, base, c);
-}
-
 // blockIdx.x: tile of R consecutive row entries; blockIdx.y: 128 consecutive
 // sorted columns (4 groups of 32).  Each thread owns one column and runs the
 // recurrence for all R rows of the tile at once (R independent carry chains).
 // With a work list (batched families), work item blockIdx.x names the tile
 // (at most R rows of one family) and its first column group instead.
-constexpr int tpp_min_ctas(bool parts) { return parts ? 6 : 1; }
-
-template <int W, int R, bool PARTS = false>
-__global__ void __launch_bounds__(kTppThreads, tpp_min_ctas(PARTS)) k_lcs_tpp(KParams p) {
+// The explicit minimum of one CTA per SM matters: with it ptxas keeps more
+// of a step's Peq words in flight (W = 7, R = 2: 84 registers instead of 55),
+// which measured 4-5 % faster at every width than the bare thread bound.
+template <int W, int R>
+__global__ void __launch_bounds__(kTppThreads, 1) k_lcs_tpp(KParams p) {
   extern __shared__ __align__(16) uint32_t sPeq[];  // R * W * 64 u32
   int32_t tile_e, tile_end, gbase;
   if (p.items) {
@@ -179,17 +156,13 @@ __global__ void __launch_bounds__(kTppThreads, tpp_min_ctas(PARTS)) k_lcs_tpp(KP
         const char *base = sbase + off;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          if constexpr (PARTS) {
-            lcs_step_parts<W, 0>(V[r], base + r * W * 256, 0u);
-          } else {
-            uint32_t P[2 * W];
+          uint32_t P[2 * W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-              P[2 * w] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256);
-              P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256 + 128);
-            }
-            lcs_step<W>(V[r], P);
+          for (int w = 0; w < W; ++w) {
+            P[2 * w] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256);
+            P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + (r * W + w) * 256 + 128);
           }
+          lcs_step<W>(V[r], P);
         }
       }
     }
@@ -207,6 +180,103 @@ __global__ void __launch_bounds__(kTppThreads, tpp_min_ctas(PARTS)) k_lcs_tpp(KP
     for (int i = 0; i < 2 * W; ++i) L += __popc(~V[r][i]);
     emit_lcs(p, e, p.row_id[e], t, L);
   }
+}
+
+// ------------------------------------------------------------ sliced pairs
+// Rows too wide for one thread's registers are split into G slices of WL
+// words; warp s of a CTA holds words [s*WL, (s+1)*WL) of the row's vector for
+// the 32 columns of one group, so every lane of a warp reads the same Peq
+// word (conflict free, as in thread-per-pair).  The add's carry crosses from
+// slice s to s+1: warp s runs chunk q (16 symbols) of the columns at
+// iteration q + s, collects the 16 carries out of its top word in a mask
+// (bit 15 - j for symbol j), and after the CTA barrier warp s+1 takes them
+// back in the same order as the carries into its bottom word.  Each step
+// costs two operations beyond the recurrence's 6 per word, and each chunk
+// one barrier; a CTA runs nch + G - 1 chunk iterations for nch chunks.
+// Words past the row's length have Peq 0, so they stay all ones whatever
+// carry arrives: the zero bits of all slices count the LCS.
+constexpr int kSliceWords = 16;  // default words per slice (the largest instance)
+constexpr int kSliceMaxG = 16;   // slices per CTA: 512 threads
+constexpr int kSliceMaxW = kSliceWords * kSliceMaxG;  // 256 words = 16,384 residues
+constexpr int kSliceMinW = 24;   // rows of at least this many words are sliced by default
+
+template <int WL>
+__global__ void __launch_bounds__(32 * kSliceMaxG, 1) k_lcs_slice(KParams p) {
+  extern __shared__ __align__(16) uint32_t sSl[];
+  const int G = (int)(blockDim.x >> 5);
+  int32_t e, grp;
+  if (p.items) {
+    const int4 it = p.items[blockIdx.x];
+    e = it.x;
+    grp = it.z;
+  } else {
+    e = p.e0 + (int32_t)blockIdx.x;
+    grp = (int32_t)blockIdx.y;
+  }
+  const int32_t rid = p.row_id[e];
+  const int32_t col_limit = p.triangle ? rid : p.n_cols;
+  if (grp >= p.n_groups || grp * kGroup >= col_limit) return;  // uniform over the CTA
+  const int32_t Wr = (p.row_len[e] + 63) / 64;
+  uint32_t *sPeq = sSl;                               // G * WL words x 64 u32
+  uint32_t *sMask = sSl + G * WL * kPeqWordU32;       // [2][G][32] carry masks
+  uint32_t *sSum = sMask + 2 * G * kGroup;            // [G][32] partial counts
+  const uint4 *prow = reinterpret_cast<const uint4 *>(p.peq + p.row_peq_off[e] * kPeqWordU32);
+  for (int i = threadIdx.x; i < G * WL * 16; i += blockDim.x) {
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if ((i >> 4) < Wr) v = prow[i];
+    reinterpret_cast<uint4 *>(sPeq)[i] = v;
+  }
+  __syncthreads();
+
+  const int s = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  uint32_t V[2 * WL];
+#pragma unroll
+  for (int i = 0; i < 2 * WL; ++i) V[i] = 0xffffffffu;
+  const uint4 *src = reinterpret_cast<const uint4 *>(p.colres + p.group_off[grp]) + lane;
+  const int32_t nch = p.group_chunks[grp];
+  const char *sbase = reinterpret_cast<const char *>(sPeq + s * WL * kPeqWordU32);
+  uint4 cur = __ldg(src);
+  for (int32_t it = 0; it < nch + G - 1; ++it) {
+    const int32_t q = it - s;
+    if (q >= 0 && q < nch) {  // uniform over the warp
+      uint32_t cin = s > 0 ? sMask[((it + 1) & 1) * G * kGroup + (s - 1) * kGroup + lane] : 0u;
+      uint32_t cout = 0;
+      uint4 nxt = cur;
+      if (q + 1 < nch) nxt = __ldg(src + (int64_t)(q + 1) * kGroup);
+      const uint32_t cw[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const char *base = sbase + ((cw[j] >> (8 * b)) & 0xffu);  // 4 * symbol
+          uint32_t P[2 * WL];
+#pragma unroll
+          for (int w = 0; w < WL; ++w) {
+            P[2 * w] = *reinterpret_cast<const uint32_t *>(base + w * 256);
+            P[2 * w + 1] = *reinterpret_cast<const uint32_t *>(base + w * 256 + 128);
+          }
+          LcsSlice<WL>::run(V, P, cin, cout);
+        }
+      }
+      sMask[(it & 1) * G * kGroup + s * kGroup + lane] = cout << 16;
+      cur = nxt;
+    }
+    __syncthreads();
+  }
+  int32_t L = 0;
+#pragma unroll
+  for (int i = 0; i < 2 * WL; ++i) L += __popc(~V[i]);
+  sSum[s * kGroup + lane] = (uint32_t)L;
+  __syncthreads();
+  if (s != 0) return;
+  for (int j = 1; j < G; ++j) L += (int32_t)sSum[j * kGroup + lane];
+  const int32_t t = grp * kGroup + lane;
+  if (t < p.n_cols) emit_lcs(p, e, rid, t, L);
+}
+
+// shared memory of a slice launch: the row's planes, two mask buffers, the partial counts
+constexpr size_t slice_smem(int WL, int G) {
+  return (size_t)G * WL * kPeqWordU32 * 4 + (size_t)3 * G * kGroup * 4;
 }
 
 // ------------------------------------------------------------ warp per pair
@@ -286,9 +356,6 @@ __global__ void __launch_bounds__(kWppThreads) k_lcs_wpp(KParams p) {
   }
 }
 
-// whether rows of 24..28 words take the step in parts (lcs.cu; on by default)
-bool tpp_parts_enabled();
-
 // per-width launchers (defined in the lcs_tpp_*.cu / lcs_wpp.cu units)
 // thread-per-pair launch with R rows per tile (tpp_rows_allowed(W, R))
 cudaError_t launch_tpp(int W, int R, const KParams &p, dim3 grid, cudaStream_t st);
@@ -296,5 +363,18 @@ cudaError_t launch_tpp(int W, int R, const KParams &p, dim3 grid, cudaStream_t s
 int tpp_rows(int W);
 void set_tpp_rows(int W, int R);
 cudaError_t launch_wpp(int NW, const KParams &p, dim3 grid, cudaStream_t st);
+// sliced launch: G slices of WL words per row, one column group per CTA (grid.y or items)
+cudaError_t launch_slice(int WL, int G, const KParams &p, dim3 grid, cudaStream_t st);
+
+// The kernel that runs rows of W words (lcs.cu): thread-per-pair (kw = W),
+// sliced (kw = words per slice, g = slices) or warp-per-pair (kw = 64-bit
+// words per lane).  Rows of one choice share a launch.
+enum LcsKind : int { kLcsTpp = 0, kLcsSlice = 1, kLcsWpp = 2 };
+struct LcsChoice {
+  int kind, kw, g;
+  bool operator==(const LcsChoice &o) const { return kind == o.kind && kw == o.kw && g == o.g; }
+  bool operator!=(const LcsChoice &o) const { return !(*this == o); }
+};
+LcsChoice lcs_choice(int W);
 
 }  // namespace famsa

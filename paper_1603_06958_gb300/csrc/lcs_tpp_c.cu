@@ -8,12 +8,6 @@ namespace famsa {
 template <int W, int R>
 static cudaError_t go(const KParams &p, dim3 grid, cudaStream_t st) {
   size_t smem = (size_t)R * W * kPeqWordU32 * sizeof(uint32_t);
-  if constexpr (R == 1 && tpp_use_parts(W)) {
-    if (tpp_parts_enabled()) {
-      k_lcs_tpp<W, R, true><<<grid, kTppThreads, smem, st>>>(p);
-      return cudaGetLastError();
-    }
-  }
   k_lcs_tpp<W, R><<<grid, kTppThreads, smem, st>>>(p);
   return cudaGetLastError();
 }

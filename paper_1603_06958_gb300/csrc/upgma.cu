@@ -1,21 +1,27 @@
-// famsa_upgma_tree: UPGMA over the family's LCS distances.
+// famsa_upgma_tree, famsa_nj_tree: UPGMA and neighbour joining over the
+// family's LCS distances.
 //
-// FAMSA Methods, "Determination of the guide tree": UPGMA is one of the
-// guide trees the paper names beside single linkage, and the one it sets
-// against SLINK for memory -- it needs the whole O(k^2) distance matrix,
-// which 288 GB of HBM holds for families of tens of thousands.
+// FAMSA Methods, "Determination of the guide tree": UPGMA and neighbour
+// joining are the guide trees the paper names beside single linkage, and it
+// sets them against SLINK for memory -- they need the whole O(k^2) distance
+// matrix, which 288 GB of HBM holds for families of tens of thousands.
 //
 // Distances are indel^2 / LCS as doubles (one correctly rounded division;
-// +inf for LCS = 0).  Every step takes the pair of live clusters in slots
-// a < b with the smallest (d, a, b), keeps the merged cluster in slot a, and
-// sets d(a, c) = (n_a * d(a, c) + n_b * d(b, c)) / (n_a + n_b) with each
-// operation rounded on its own (no fused multiply-add), so the result is the
-// plain sequential algorithm's bit for bit.
+// +inf for LCS = 0).  UPGMA: every step takes the pair of live clusters in
+// slots a < b with the smallest (d, a, b), keeps the merged cluster in slot
+// a, and sets d(a, c) = (n_a * d(a, c) + n_b * d(b, c)) / (n_a + n_b) with
+// each operation rounded on its own (no fused multiply-add), so the result
+// is the plain sequential algorithm's bit for bit.
 //
-// Per row i the state keeps its smallest (d(i, j), j) over live j > i.  A
-// step reads the smallest row minimum, rewrites row and column a, and then
+// Per row i the UPGMA state keeps its smallest (d(i, j), j) over live j > i.
+// A step reads the smallest row minimum, rewrites row and column a, and then
 // only rows whose minimum pointed at a or b, or that now see a smaller value
 // at a, change; those pointing at a or b (usually few) are rescanned.
+//
+// Neighbour joining recomputes every live row's sum R(i) (one thread per
+// row, adding in increasing j as the sequential algorithm does) and every
+// pair's Q(a, b) = (r - 2) d(a, b) - R(a) - R(b) per step, so a step is
+// O(k^2) and the tree O(k^3); the FP64 rate bounds it.
 #include <algorithm>
 #include <cmath>
 
@@ -24,6 +30,8 @@
 using namespace famsa;
 
 namespace {
+
+constexpr int32_t kNjMaxK = 32768;  // O(k^3) time: about a minute at this size
 
 struct Upgma {
   double *D;         // k x k
@@ -183,7 +191,199 @@ __global__ void k_up_init(Upgma U) {
   if (i == 0) { U.ctl[0] = 0; U.ctl[1] = -1; U.ctl[2] = -1; U.ctl[3] = 0; }
 }
 
+
+// ------------------------------------------------------------ neighbour joining
+struct Nj {
+  double *D;        // k x k, symmetric
+  double *R;        // per live slot: the sum of its distances to the other live slots
+  double *rq;       // per row i: smallest Q(i, j) over live j > i
+  int32_t *rj;      // its j (-1: none)
+  int32_t *n;       // cluster sizes per slot
+  int32_t *id;      // cluster id per slot
+  uint8_t *live;
+  int32_t *ctl;     // [0] a, [1] b, [2] an infinite distance seen
+  double *dab;      // d(a, b) of the step
+  int32_t *merges;
+  double *lengths;
+  int32_t *sizes;
+  int32_t k;
+};
+
+__global__ void k_nj_init(Nj J) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < J.k) { J.n[i] = 1; J.id[i] = i; J.live[i] = 1; }
+  if (i == 0) { J.ctl[0] = -1; J.ctl[1] = -1; J.ctl[2] = 0; }
+}
+
+// neighbour joining is undefined with an infinite distance (a pair with LCS 0)
+__global__ void k_nj_check(Nj J) {
+  const int64_t total = (int64_t)J.k * J.k;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x)
+    if (isinf(J.D[x])) J.ctl[2] = 1;
+}
+
+// R(i) over live j != i in increasing j (thread i reads column i: coalesced
+// across threads, and equal to row i since D is exactly symmetric)
+__global__ void k_nj_rsum(Nj J) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= J.k || !J.live[i]) return;
+  double s = 0.0;
+  for (int32_t j = 0; j < J.k; ++j)
+    if (J.live[j] && j != i) s = __dadd_rn(s, J.D[(int64_t)j * J.k + i]);
+  J.R[i] = s;
+}
+
+__device__ __forceinline__ bool q_lt(double v1, int32_t j1, double v2, int32_t j2) {
+  if (j2 < 0) return j1 >= 0;
+  if (j1 < 0) return false;
+  return v1 < v2 || (v1 == v2 && j1 < j2);
+}
+
+// row i: the smallest (Q(i, j), j) over live j > i, one CTA per row
+__global__ void k_nj_qrow(Nj J, double rm2) {
+  __shared__ double sv[32];
+  __shared__ int32_t sj[32];
+  const int32_t i = blockIdx.x;
+  if (!J.live[i]) {
+    if (threadIdx.x == 0) J.rj[i] = -1;
+    return;
+  }
+  const double Ri = J.R[i];
+  const double *row = J.D + (int64_t)i * J.k;
+  double bv = 0.0;
+  int32_t bj = -1;
+  for (int32_t j = i + 1 + threadIdx.x; j < J.k; j += blockDim.x) {
+    if (!J.live[j]) continue;
+    const double q = __dsub_rn(__dsub_rn(__dmul_rn(rm2, row[j]), Ri), J.R[j]);
+    if (q_lt(q, j, bv, bj)) { bv = q; bj = j; }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 16; d > 0; d >>= 1) {
+    const double v2 = __shfl_down_sync(0xffffffffu, bv, d);
+    const int32_t j2 = __shfl_down_sync(0xffffffffu, bj, d);
+    if (q_lt(v2, j2, bv, bj)) { bv = v2; bj = j2; }
+  }
+  if (lane == 0) { sv[warp] = bv; sj[warp] = bj; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (q_lt(sv[w], sj[w], bv, bj)) { bv = sv[w]; bj = sj[w]; }
+    J.rq[i] = bv;
+    J.rj[i] = bj;
+  }
+}
+
+// record step t: the pair (a, b) with the smallest (Q, a, b) (or, with two
+// clusters left, the two), its branch lengths, and slot a takes the new cluster
+__global__ void k_nj_pick(Nj J, int32_t t, int32_t r) {
+  __shared__ double sv[32];
+  __shared__ int32_t sa[32], sb[32];
+  double bv = 0.0;
+  int32_t ba = -1, bb = -1;
+  if (r > 2) {
+    for (int32_t i = threadIdx.x; i < J.k; i += blockDim.x) {
+      const int32_t j = J.live[i] ? J.rj[i] : -1;
+      if (j < 0) continue;
+      const double v = J.rq[i];
+      if (ba < 0 || v < bv || (v == bv && (i < ba || (i == ba && j < bb)))) { bv = v; ba = i; bb = j; }
+    }
+  } else {
+    for (int32_t i = threadIdx.x; i < J.k; i += blockDim.x)
+      if (J.live[i] && (ba < 0 || i < ba)) { ba = i; bb = 0; }  // the lowest live slot per thread
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 16; d > 0; d >>= 1) {
+    const double v2 = __shfl_down_sync(0xffffffffu, bv, d);
+    const int32_t a2 = __shfl_down_sync(0xffffffffu, ba, d), b2 = __shfl_down_sync(0xffffffffu, bb, d);
+    if (a2 >= 0 && (ba < 0 || v2 < bv || (v2 == bv && (a2 < ba || (a2 == ba && b2 < bb))))) { bv = v2; ba = a2; bb = b2; }
+  }
+  if (lane == 0) { sv[warp] = bv; sa[warp] = ba; sb[warp] = bb; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    const double v2 = sv[w];
+    const int32_t a2 = sa[w], b2 = sb[w];
+    if (a2 >= 0 && (ba < 0 || v2 < bv || (v2 == bv && (a2 < ba || (a2 == ba && b2 < bb))))) { bv = v2; ba = a2; bb = b2; }
+  }
+  double da, db;
+  if (r > 2) {
+    const double dab = J.D[(int64_t)ba * J.k + bb];
+    da = __dadd_rn(__dmul_rn(dab, 0.5), __ddiv_rn(__dsub_rn(J.R[ba], J.R[bb]), (double)(2 * (r - 2))));
+    db = __dsub_rn(dab, da);
+    *J.dab = dab;
+  } else {
+    bb = -1;  // the other live slot: the first above ba
+    for (int32_t i = ba + 1; i < J.k && bb < 0; ++i)
+      if (J.live[i]) bb = i;
+    da = __dmul_rn(J.D[(int64_t)ba * J.k + bb], 0.5);
+    db = da;
+  }
+  const int32_t ia = J.id[ba], ib = J.id[bb];
+  const bool lo_a = ia < ib;
+  J.merges[2 * t] = lo_a ? ia : ib;
+  J.merges[2 * t + 1] = lo_a ? ib : ia;
+  J.lengths[2 * t] = lo_a ? da : db;
+  J.lengths[2 * t + 1] = lo_a ? db : da;
+  J.n[ba] += J.n[bb];
+  J.sizes[t] = J.n[ba];
+  J.id[ba] = J.k + t;
+  J.live[bb] = 0;
+  J.ctl[0] = ba;
+  J.ctl[1] = bb;
+}
+
+// row and column a of the new cluster: d(a, c) = (d(a, c) + d(b, c) - d(a, b)) / 2
+__global__ void k_nj_merge(Nj J) {
+  const int32_t a = J.ctl[0], b = J.ctl[1];
+  const double dab = *J.dab;
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < J.k; c += gridDim.x * blockDim.x) {
+    if (!J.live[c] || c == a || c == b) continue;
+    const double v = __dmul_rn(__dsub_rn(__dadd_rn(J.D[(int64_t)a * J.k + c], J.D[(int64_t)b * J.k + c]), dab), 0.5);
+    J.D[(int64_t)a * J.k + c] = v;
+    J.D[(int64_t)c * J.k + a] = v;
+  }
+}
+
 }  // namespace
+
+// all pairs' LCS in caller labels (the i < j triangle), then the k x k distances
+static cudaError_t family_distances(Family *f, Scratch &sc, double *D, int32_t *d_iota) {
+  const int32_t k = f->k;
+  cudaStream_t st = sc.st;
+  int32_t *tri = sc.get<int32_t>((size_t)k * (k - 1) / 2);
+  if (sc.err != cudaSuccess) return sc.err;
+  std::vector<int32_t> h_w(k), h_id(k);
+  for (int32_t s = 0; s < k; ++s) { h_w[s] = (f->h_slen[s] + 63) / 64; h_id[s] = s; }
+  cudaError_t err = cudaMemcpyAsync(d_iota, h_id.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st);
+  LcsBatch b;
+  b.peq = f->d_peq;
+  b.colres = f->d_colres;
+  b.group_off = f->d_group_off;
+  b.group_chunks = f->d_group_chunks;
+  b.col_perm = f->d_perm;
+  b.col_len = f->d_slen;
+  b.n_cols = k;
+  b.k = k;
+  b.row_peq_off = f->d_peq_off;
+  b.row_len = f->d_slen;
+  b.row_id = d_iota;
+  b.row_orig = f->d_perm;
+  b.n_rows = k;
+  b.h_row_w = h_w.data();
+  b.h_row_id = h_id.data();
+  b.mode = kOutTriOrig;
+  b.out = tri;
+  b.triangle = true;
+  int64_t launches = 0;
+  if (err == cudaSuccess) err = launch_lcs(b, st, &launches);
+  if (err == cudaSuccess) {
+    k_up_dist<<<152 * 16, 256, 0, st>>>(tri, f->d_len, k, D);
+    err = cudaGetLastError();
+  }
+  // the host vectors above are read by the copy: wait before they go
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  return err;
+}
 
 extern "C" int famsa_upgma_tree(const famsa_family *fh, int32_t *merges, double *heights, int32_t *sizes,
                                 int on_device, void *cuda_stream) {
@@ -198,8 +398,6 @@ extern "C" int famsa_upgma_tree(const famsa_family *fh, int32_t *merges, double 
   sc.st = st;
   Upgma U;
   U.k = k;
-  const int64_t npairs = (int64_t)k * (k - 1) / 2;
-  int32_t *tri = sc.get<int32_t>((size_t)npairs);
   U.D = sc.get<double>((size_t)k * k);
   U.rval = sc.get<double>(k);
   U.rarg = sc.get<int32_t>(k);
@@ -214,47 +412,20 @@ extern "C" int famsa_upgma_tree(const famsa_family *fh, int32_t *merges, double 
   U.heights = on_device ? heights : sc.get<double>((size_t)(k - 1));
   U.sizes = on_device ? sizes : sc.get<int32_t>((size_t)(k - 1));
   cudaError_t err = sc.err;
+  if (err == cudaSuccess) err = family_distances(f, sc, U.D, d_iota);
   if (err == cudaSuccess) {
-    // all pairs' LCS in caller labels (the i < j triangle), then the distances
-    std::vector<int32_t> h_w(k), h_id(k);
-    for (int32_t s = 0; s < k; ++s) { h_w[s] = (f->h_slen[s] + 63) / 64; h_id[s] = s; }
-    err = cudaMemcpyAsync(d_iota, h_id.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st);
-    LcsBatch b;
-    b.peq = f->d_peq;
-    b.colres = f->d_colres;
-    b.group_off = f->d_group_off;
-    b.group_chunks = f->d_group_chunks;
-    b.col_perm = f->d_perm;
-    b.col_len = f->d_slen;
-    b.n_cols = k;
-    b.k = k;
-    b.row_peq_off = f->d_peq_off;
-    b.row_len = f->d_slen;
-    b.row_id = d_iota;
-    b.row_orig = f->d_perm;
-    b.n_rows = k;
-    b.h_row_w = h_w.data();
-    b.h_row_id = h_id.data();
-    b.mode = kOutTriOrig;
-    b.out = tri;
-    b.triangle = true;
-    int64_t launches = 0;
-    if (err == cudaSuccess) err = launch_lcs(b, st, &launches);
-    if (err == cudaSuccess) {
-      k_up_dist<<<152 * 16, 256, 0, st>>>(tri, f->d_len, k, U.D);
-      const unsigned nb = (unsigned)((k + 255) / 256);
-      k_up_init<<<nb, 256, 0, st>>>(U);
-      k_up_rowmin_all<<<(unsigned)k, 256, 0, st>>>(U);
-      for (int32_t t = 0; t + 1 < k && err == cudaSuccess; ++t) {
-        k_up_pick<<<1, 1024, 0, st>>>(U);
-        k_up_merge<<<std::min<unsigned>(nb, 152), 256, 0, st>>>(U);
-        k_up_book<<<1, 1, 0, st>>>(U);
-        k_up_fix<<<nb, 256, 0, st>>>(U);
-        k_up_rescan<<<152, 256, 0, st>>>(U);
-        if ((t & 1023) == 0) err = cudaGetLastError();
-      }
-      if (err == cudaSuccess) err = cudaGetLastError();
+    const unsigned nb = (unsigned)((k + 255) / 256);
+    k_up_init<<<nb, 256, 0, st>>>(U);
+    k_up_rowmin_all<<<(unsigned)k, 256, 0, st>>>(U);
+    for (int32_t t = 0; t + 1 < k && err == cudaSuccess; ++t) {
+      k_up_pick<<<1, 1024, 0, st>>>(U);
+      k_up_merge<<<std::min<unsigned>(nb, 152), 256, 0, st>>>(U);
+      k_up_book<<<1, 1, 0, st>>>(U);
+      k_up_fix<<<nb, 256, 0, st>>>(U);
+      k_up_rescan<<<152, 256, 0, st>>>(U);
+      if ((t & 1023) == 0) err = cudaGetLastError();
     }
+    if (err == cudaSuccess) err = cudaGetLastError();
   }
   if (err == cudaSuccess && !on_device) {
     err = cudaMemcpyAsync(merges, U.merges, sizeof(int32_t) * 2 * (size_t)(k - 1), cudaMemcpyDeviceToHost, st);
@@ -266,5 +437,70 @@ extern "C" int famsa_upgma_tree(const famsa_family *fh, int32_t *merges, double 
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   else cudaStreamSynchronize(st);
   sc.release();
+  return status_from_cuda(err);
+}
+
+extern "C" int famsa_nj_tree(const famsa_family *fh, int32_t *merges, double *lengths, int32_t *sizes,
+                             int on_device, void *cuda_stream) {
+  if (!fh || !merges || !lengths || !sizes) return FAMSA_EINVAL;
+  Family *f = const_cast<Family *>(reinterpret_cast<const Family *>(fh));
+  const int32_t k = f->k;
+  if (k < 2) return FAMSA_OK;
+  if (k > kNjMaxK) return FAMSA_ERANGE;
+  std::lock_guard<std::mutex> lk(f->mu);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Scratch sc;
+  sc.st = st;
+  Nj J;
+  J.k = k;
+  J.D = sc.get<double>((size_t)k * k);
+  J.R = sc.get<double>(k);
+  J.rq = sc.get<double>(k);
+  J.rj = sc.get<int32_t>(k);
+  J.n = sc.get<int32_t>(k);
+  J.id = sc.get<int32_t>(k);
+  J.live = sc.get<uint8_t>(k);
+  J.ctl = sc.get<int32_t>(3);
+  J.dab = sc.get<double>(1);
+  int32_t *d_iota = sc.get<int32_t>(k);
+  J.merges = on_device ? merges : sc.get<int32_t>(2 * (size_t)(k - 1));
+  J.lengths = on_device ? lengths : sc.get<double>(2 * (size_t)(k - 1));
+  J.sizes = on_device ? sizes : sc.get<int32_t>((size_t)(k - 1));
+  cudaError_t err = sc.err;
+  if (err == cudaSuccess) err = family_distances(f, sc, J.D, d_iota);
+  int32_t inf = 0;
+  if (err == cudaSuccess) {
+    const unsigned nb = (unsigned)((k + 255) / 256);
+    k_nj_init<<<nb, 256, 0, st>>>(J);
+    k_nj_check<<<152 * 8, 256, 0, st>>>(J);
+    err = cudaMemcpyAsync(&inf, J.ctl + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  }
+  if (err == cudaSuccess && !inf) {
+    const unsigned nr = (unsigned)((k + 63) / 64);
+    const unsigned nm = std::min<unsigned>((unsigned)((k + 255) / 256), 152);
+    for (int32_t t = 0; t + 1 < k && err == cudaSuccess; ++t) {
+      const int32_t r = k - t;
+      if (r > 2) {
+        k_nj_rsum<<<nr, 64, 0, st>>>(J);
+        k_nj_qrow<<<(unsigned)k, 256, 0, st>>>(J, (double)(r - 2));
+      }
+      k_nj_pick<<<1, 1024, 0, st>>>(J, t, r);
+      if (r > 2) k_nj_merge<<<nm, 256, 0, st>>>(J);
+      if ((t & 1023) == 0) err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaGetLastError();
+  }
+  if (err == cudaSuccess && !inf && !on_device) {
+    err = cudaMemcpyAsync(merges, J.merges, sizeof(int32_t) * 2 * (size_t)(k - 1), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(lengths, J.lengths, sizeof(double) * 2 * (size_t)(k - 1), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(sizes, J.sizes, sizeof(int32_t) * (size_t)(k - 1), cudaMemcpyDeviceToHost, st);
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  else cudaStreamSynchronize(st);
+  sc.release();
+  if (err == cudaSuccess && inf) return FAMSA_ERANGE;
   return status_from_cuda(err);
 }

@@ -74,6 +74,8 @@ def test_argument_errors_without_device_work(lib):
     assert lib.famsa_family_size(None) == -1
     lib.famsa_free(None)
     assert lib.famsa_debug_set_tpp_max_w(99) == fg.FAMSA_EINVAL
+    assert lib.famsa_debug_set_slices(-1, 0) == fg.FAMSA_EINVAL
+    assert lib.famsa_debug_set_slices(1, 17) == fg.FAMSA_EINVAL
     assert lib.famsa_debug_set_cluster(3) == fg.FAMSA_EINVAL
     assert lib.famsa_server_cancel(None, 0) == fg.FAMSA_EINVAL
 

@@ -1,6 +1,6 @@
 """GPU parity of the LCS kernels against the oracle's DP (bit-exact, int32).
 
-Covers thread-per-pair and warp-per-pair kernels at every word boundary,
+Covers thread-per-pair, sliced and warp-per-pair kernels at every word boundary,
 ragged tails, tie-heavy small alphabets, ambiguity codes, host and device
 buffers, row bands, query scoring and the error paths of the C ABI.
 """
@@ -21,6 +21,7 @@ def fg():
     m.load()
     yield m
     m.debug_set_tpp_max_w(32)
+    m.debug_set_slices(24, 0)
 
 
 def family_from(seqs):
@@ -67,13 +68,29 @@ def test_allpairs_word_boundaries(fg, alphabet):
 
 @pytest.mark.parametrize("tmax", [0, 1, 2, 5])
 def test_warp_per_pair_matches(fg, tmax):
-    # rows wider than tmax words go through the warp-per-pair kernel
+    # with slices off, rows wider than tmax words go through the warp-per-pair kernel
     fg.debug_set_tpp_max_w(tmax)
+    fg.debug_set_slices(0)
     try:
         res, off = boundary_family(40 + tmax)
         check_allpairs(fg, res, off)
     finally:
         fg.debug_set_tpp_max_w(32)
+        fg.debug_set_slices(24, 0)
+
+
+@pytest.mark.parametrize("min_w,words", [(1, 1), (1, 2), (2, 3), (1, 5), (1, 16), (24, 0)])
+def test_sliced_matches(fg, min_w, words):
+    # rows of at least min_w words split over warps of at most `words` words:
+    # one slice (W <= words), two, and up to 16 (W = 47 in slices of 3); the
+    # carries cross slices at every word boundary of the family's lengths
+    fg.debug_set_slices(min_w, words)
+    try:
+        for alphabet in (25, 2):
+            res, off = boundary_family(60 + min_w + words + alphabet, alphabet, extra=(1300, 1344, 1345))
+            check_allpairs(fg, res, off)
+    finally:
+        fg.debug_set_slices(24, 0)
 
 
 @pytest.mark.parametrize("rows", [1, 2, 4])
@@ -90,10 +107,13 @@ def test_rows_per_tile_choices(fg, rows):
             fg.debug_set_tpp_rows(w, 0)
 
 
-def test_long_sequences_warp_per_pair_default(fg):
+def test_long_sequences_default_kernels(fg):
+    # rows of 33..141 words take the sliced kernel (2 to 9 slices), the one of
+    # 16,385 residues (257 words) warp-per-pair
     rng = np.random.default_rng(9)
-    seqs = [rng.integers(0, 20, n).astype(np.uint8) for n in (2100, 4096, 4097, 6000, 100, 9000)]
+    seqs = [rng.integers(0, 20, n).astype(np.uint8) for n in (2100, 4096, 4097, 6000, 100, 9000, 16385)]
     seqs.append(seqs[3][::2].copy())
+    seqs.append(np.concatenate([seqs[5], seqs[3][:7385]]))  # shares 9,000 + residues with two rows
     res, off = family_from(seqs)
     check_allpairs(fg, res, off)
 
@@ -201,10 +221,10 @@ def test_plain20k_sampled_pairs(fg):
     assert np.array_equal(sample, want)
 
 
-@pytest.mark.parametrize("parts", [1, 0])
-def test_wide_rows_in_parts(fg, parts):
-    # rows of 23..29 words: 24..28 take the step in parts with the carry in a
-    # register (unless switched off); both forms equal the oracle
+@pytest.mark.parametrize("slices", [24, 0])
+def test_wide_rows_sliced_or_whole(fg, slices):
+    # rows of 23..29 words: from 24 words on they run sliced by default, with
+    # slices off thread-per-pair takes them whole; both forms equal the oracle
     rng = np.random.default_rng(77)
     base = rng.integers(0, 20, 1900).astype(np.uint8)
     seqs = []
@@ -214,11 +234,11 @@ def test_wide_rows_in_parts(fg, parts):
         s[flip] = rng.integers(0, 20, int(flip.sum()))
         seqs.append(s)
     res, off = family_from(seqs)
-    fg.debug_set_tpp_parts(parts)
+    fg.debug_set_slices(slices)
     try:
         fam = fg.pack_peq(res, off)
         got = np.asarray(fg.lcs_allpairs(fam))
         fam.free()
     finally:
-        fg.debug_set_tpp_parts(1)
+        fg.debug_set_slices(24, 0)
     assert np.array_equal(got, oracle.lcs_allpairs(res, off))
