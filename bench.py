@@ -629,7 +629,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = OPS_PER_WORD_STEP * word_steps / (lcs_ms * 1e-3) / 1e12
     peak = SMS * ALU_LANES * SM_MAX_GHZ * 1e9 / 1e12
     peak_all = SMS * INT32_LANES * SM_MAX_GHZ * 1e9 / 1e12
-    tr = recorded_traffic()
+    # the DRAM record is of the plain k=20,000 family's LCS launches: it
+    # applies to that workload only
+    tr = recorded_traffic() if args.workload == "plain20k" and args.k is None and args.seed == 1 else None
     line = {
         "metric": METRIC,
         "value": cells_total / (ms_step_max * 1e-3) / 1e9,

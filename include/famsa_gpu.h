@@ -517,8 +517,8 @@ void famsa_free(famsa_family *f);
  *   LCS kernels in ns (CUDA events around each row block), 8 device time of
  *   the row-update kernels in ns, 9 device time of the finalisation in ns,
  *   10 LCS kernel launches, 11 kernel launches of famsa_pack_peq for this
- *   handle, 12 row-update kernel (1 cluster shared memory, 2 global memory),
- *   13 its cluster size, 14..17 kilocycles spent by one thread of the
+ *   handle, 12 row update (1 insertion in cluster shared memory, 2 insertion
+ *   in global memory, 3 spanning-tree rebuild), 13 the cluster size of 1, 14..17 kilocycles spent by one thread of the
  *   shared-memory kernel in its phases (14 unused; 15 scans, pointer update
  *   and prefetch; 16 shift re-layout plus the next point's distances;
  *   17 run-merge re-layout), 18 1 when keys were exact order codes (every

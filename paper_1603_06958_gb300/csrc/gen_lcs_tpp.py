@@ -45,8 +45,11 @@ def slice_unit(name, widths):
              "template <int WL>",
              "static cudaError_t go(int G, const KParams &p, dim3 grid, cudaStream_t st) {",
              "  const size_t smem = slice_smem(WL, G);",
-             "  if (smem > 48 * 1024) {",
-             "    cudaError_t e = cudaFuncSetAttribute(k_lcs_slice<WL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
+             "  // the cap is per kernel: the largest any launch of it needs (16 slices),",
+             "  // so that launches from other threads never lower it under this one",
+             "  const size_t smem_max = slice_smem(WL, kSliceMaxG);",
+             "  if (smem_max > 48 * 1024) {",
+             "    cudaError_t e = cudaFuncSetAttribute(k_lcs_slice<WL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);",
              "    if (e != cudaSuccess) return e;",
              "  }",
              "  k_lcs_slice<WL><<<grid, 32 * G, smem, st>>>(p);",

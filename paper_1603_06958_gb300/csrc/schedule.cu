@@ -140,7 +140,10 @@ extern "C" int famsa_progressive_schedule(int32_t k, const int32_t *merges, cons
   }
   const int use_smem = n <= kSchedSmem;
   const size_t smem = sizeof(int32_t) * (2 * kSchedChunk + (use_smem ? (size_t)n : 0));
-  cudaError_t err = cudaFuncSetAttribute(k_sched_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the cap is per kernel: set the largest any call needs, so that calls on
+  // other streams never lower it under this launch
+  const size_t smem_max = sizeof(int32_t) * (2 * kSchedChunk + (size_t)kSchedSmem);
+  cudaError_t err = cudaFuncSetAttribute(k_sched_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
   if (err == cudaSuccess) {
     k_sched_levels<<<1, kSchedThreads, smem, st>>>(k, dm, dl, ctl, ctl + 1, use_smem);
     k_sched_kind<<<nb(n, 256), 256, 0, st>>>(k, dm, ds, dk);

@@ -589,7 +589,10 @@ cudaError_t launch_msf_leaf_order(const MsfState &S, int32_t k, int32_t *ord, ui
   ++L;
   if (k <= kKrtSmemMax) {
     const size_t smem = 2 * sizeof(int32_t) * kKrtChunk + 5 * sizeof(uint16_t) * (size_t)k;
-    cudaError_t e = cudaFuncSetAttribute(k_msf_krt_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the cap is per kernel, not per launch: set it to the largest size any
+    // call needs, so that calls on other streams never lower it under a launch
+    const size_t smem_max = 2 * sizeof(int32_t) * kKrtChunk + 5 * sizeof(uint16_t) * (size_t)kKrtSmemMax;
+    cudaError_t e = cudaFuncSetAttribute(k_msf_krt_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return e;
     k_msf_krt_smem<<<1, kKrtThreads, smem, st>>>(k, ea, eb, gidx, ord, gi, S.ctl);
   } else {

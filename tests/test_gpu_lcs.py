@@ -147,18 +147,22 @@ def test_ambiguity_and_scale_alphabet(fg):
     check_allpairs(fg, res, off)
 
 
-def test_rows_band(fg):
-    res, off = synth.family(400, 3, root_len=120, alphabet=0, ext_frac=0.2)
+@pytest.mark.parametrize("k,root_len", [(400, 120), (120, 1800)])
+def test_rows_band(fg, k, root_len):
+    # short rows (thread-per-pair) and rows of 24-32 words (sliced kernel)
+    res, off = synth.family(k, 3, root_len=root_len, alphabet=0, ext_frac=0.2)
     fam = fg.pack_peq(res, off)
-    for r0, r1 in ((0, 1), (0, 5), (37, 61), (390, 400), (0, 400)):
+    for r0, r1 in ((0, 1), (0, 5), (37, 61), (k - 10, k), (0, k)):
         got = fg.lcs_rows(fam, r0, r1)
         want = oracle.lcs_rows(res, off, r0, r1)
         assert np.array_equal(got, want), (r0, r1)
 
 
-def test_query(fg):
+@pytest.mark.parametrize("qlen", [180, 2000])
+def test_query(fg, qlen):
+    # queries of 3 words (thread-per-pair) and of about 32 words (sliced)
     res, off = synth.family(300, 4, root_len=200)
-    q, qoff = synth.family(17, 5, root_len=180)
+    q, qoff = synth.family(17, 5, root_len=qlen)
     fam = fg.pack_peq(res, off)
     got = fg.lcs_query(fam, q, qoff)
     k, nq = len(off) - 1, len(qoff) - 1

@@ -94,6 +94,28 @@ def test_mix_equals_alone(fg, slots, budget):
         srv.close()
 
 
+def test_concurrent_calls_of_every_size(fg):
+    # many tree requests of different sizes at once on 8 slots: their kernels
+    # that size their shared memory by the family (the leaf-order join, the
+    # sliced LCS) run side by side on different streams, and every call must
+    # still succeed and equal the call alone (a per-launch shared-memory cap
+    # set by one call must never be lowered under another's launch)
+    ks = [int(x) for x in np.geomspace(30, 16000, 24)]
+    fams = [synth.family(k, 500 + i, root_len=60 if i % 3 else 1700, indel_rate=0.002)
+            for i, k in enumerate(ks)]
+    want = [alone_tree(fg, r, o) for r, o in fams]
+    srv = fg.Server(32 << 30, 8)
+    try:
+        for rep in range(2):
+            tids = [srv.submit_tree(r, o) for r, o in fams]
+            for i, t in enumerate(tids):
+                assert srv.wait(t) == fg.FAMSA_OK, (rep, ks[i])
+                same_tree(srv.tree_result(t), want[i], (rep, ks[i]))
+                srv.release(t)
+    finally:
+        srv.close()
+
+
 def test_failures_stay_per_request(fg):
     srv = fg.Server(8 << 30, 3)
     try:
