@@ -192,12 +192,14 @@ int famsa_upgma_tree(const famsa_family *f, int32_t *merges, double *heights, in
  * famsa_nj_tree -- neighbour joining, the other guide tree the paper names
  * beside single linkage ("Determination of the guide tree"), over the same
  * distances as famsa_upgma_tree.  With r clusters live, R(i) is the sum of
- * d(i, j) over the live j != i (added in increasing j) and the live slots
- * a < b with the smallest (Q, a, b), Q = (r - 2) d(a, b) - R(a) - R(b), are
- * joined with branches delta_a = d(a, b) / 2 + (R(a) - R(b)) / (2 (r - 2))
- * and delta_b = d(a, b) - delta_a; the new cluster takes slot a with
- * d(a, c) = (d(a, c) + d(b, c) - d(a, b)) / 2.  The last two clusters are
- * joined with d(a, b) / 2 on each branch (the root).  Every operation is
+ * d(i, j) over the live j != i, and the live slots a < b with the smallest
+ * (Q, a, b), Q = (r - 2) d(a, b) - R(a) - R(b), are joined with branches
+ * delta_a = d(a, b) / 2 + (R(a) - R(b)) / (2 (r - 2)) and
+ * delta_b = d(a, b) - delta_a; the new cluster u takes slot a with
+ * d(u, c) = (d(a, c) + d(b, c) - d(a, b)) / 2.  The row sums are added in
+ * increasing j once, then follow each join: R(c) = R(c) - d(a, c) - d(b, c)
+ * + d(u, c), R(u) = (R(a) + R(b) - r d(a, b)) / 2.  The last two clusters
+ * are joined with d(a, b) / 2 on each branch (the root).  Every operation is
  * rounded on its own, in that order (no fused multiply-add).
  *   merges (2(k-1)): merge t joins cluster ids (smaller, larger), as
  *     famsa_upgma_tree.
@@ -205,8 +207,8 @@ int famsa_upgma_tree(const famsa_family *f, int32_t *merges, double *heights, in
  *     merges[2t+1] (they may be negative: neighbour joining does not
  *     prevent it).  sizes (k-1): the new cluster's size.
  * On the device iff on_device != 0; the call waits for its stream.  It holds
- * the k x k matrix of doubles on the device; each step is O(k^2) in FP64, so
- * the tree is O(k^3) (k = 8,192: about a second).
+ * the k x k matrix of doubles on the device; each step reads the live part
+ * of it once, so the tree is O(k^3).
  * Errors: EINVAL (NULL), ERANGE (k above 32,768, or a pair with LCS 0: an
  *   infinite distance, for which neighbour joining is undefined), ENOMEM,
  *   ECUDA.

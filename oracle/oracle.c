@@ -1037,18 +1037,23 @@ int oracle_upgma(int32_t k, const double *D0, int32_t *merges, double *heights, 
  * Neighbour joining (Saitou & Nei 1987, in Studier & Keppler's form), the
  * other alternative to single linkage the paper names ("Determination of
  * the guide tree"), over the same distances as UPGMA.  With r clusters live:
- *     R(i)    = sum of d(i, j) over the live j != i, added in increasing j;
+ *     R(i)    = sum of d(i, j) over the live j != i;
  *     Q(a, b) = (r - 2) * d(a, b) - R(a) - R(b);
  * the pair of live slots a < b with the smallest (Q, a, b) is joined; its
  * branches are
  *     delta_a = d(a, b) / 2 + (R(a) - R(b)) / (2 (r - 2)),  delta_b = d(a, b) - delta_a;
- * the new cluster takes slot a with d(a, c) = (d(a, c) + d(b, c) - d(a, b)) / 2
- * for every other live c.  When two clusters are left they are joined with
- * d(a, b) / 2 on each branch (the root of the guide tree).  Every operation is
- * rounded on its own, in exactly the order written (no fused multiply-add).
- * Merge t joins ids (smaller, larger) with branch lengths[2t], lengths[2t+1]
- * in that order, making a cluster of sizes[t] sequences.  NJ is undefined
- * with an infinite distance (a pair with LCS 0): returns -3 then.
+ * the new cluster u takes slot a with d(u, c) = (d(a, c) + d(b, c) - d(a, b)) / 2
+ * for every other live c.  The row sums start as sums in increasing j and
+ * then follow the joins (Studier & Keppler's update, equal in exact
+ * arithmetic to summing afresh):
+ *     R(c) = R(c) - d(a, c) - d(b, c) + d(u, c)   for every other live c,
+ *     R(u) = (R(a) + R(b) - r * d(a, b)) / 2.
+ * When two clusters are left they are joined with d(a, b) / 2 on each branch
+ * (the root of the guide tree).  Every operation is rounded on its own, in
+ * exactly the order written (no fused multiply-add).  Merge t joins ids
+ * (smaller, larger) with branch lengths[2t], lengths[2t+1] in that order,
+ * making a cluster of sizes[t] sequences.  NJ is undefined with an infinite
+ * distance (a pair with LCS 0): returns -3 then.
  */
 int oracle_nj(int32_t k, const double *D0, int32_t *merges, double *lengths, int32_t *sizes) {
   if (k < 1) return -1;
@@ -1061,7 +1066,13 @@ int oracle_nj(int32_t k, const double *D0, int32_t *merges, double *lengths, int
   char *alive = (char *)malloc((size_t)k);
   if (!D || !R || !id || !n || !alive) { free(D); free(R); free(id); free(n); free(alive); return -2; }
   memcpy(D, D0, sizeof(double) * (size_t)k * (size_t)k);
-  for (int32_t i = 0; i < k; ++i) { id[i] = i; n[i] = 1; alive[i] = 1; }
+  for (int32_t i = 0; i < k; ++i) {
+    id[i] = i; n[i] = 1; alive[i] = 1;
+    double s = 0.0;
+    for (int32_t j = 0; j < k; ++j)
+      if (j != i) s = s + D[(size_t)i * k + j];
+    R[i] = s;
+  }
   for (int32_t t = 0; t + 1 < k; ++t) {
     const int32_t r = k - t;
     int32_t ba = -1, bb = -1;
@@ -1072,13 +1083,6 @@ int oracle_nj(int32_t k, const double *D0, int32_t *merges, double *lengths, int
       da = D[(size_t)ba * k + bb] * 0.5;
       db = da;
     } else {
-      for (int32_t i = 0; i < k; ++i) {
-        if (!alive[i]) continue;
-        double s = 0.0;
-        for (int32_t j = 0; j < k; ++j)
-          if (alive[j] && j != i) s = s + D[(size_t)i * k + j];
-        R[i] = s;
-      }
       double best = 0.0;
       for (int32_t a = 0; a < k; ++a) {
         if (!alive[a]) continue;
@@ -1093,12 +1097,16 @@ int oracle_nj(int32_t k, const double *D0, int32_t *merges, double *lengths, int
       const double dab = D[(size_t)ba * k + bb];
       da = dab * 0.5 + (R[ba] - R[bb]) / (double)(2 * (r - 2));
       db = dab - da;
+      const double ru = ((R[ba] + R[bb]) - (double)r * dab) * 0.5;
       for (int32_t c = 0; c < k; ++c) {
         if (!alive[c] || c == ba || c == bb) continue;
-        double v = ((D[(size_t)ba * k + c] + D[(size_t)bb * k + c]) - dab) * 0.5;
+        const double dac = D[(size_t)ba * k + c], dbc = D[(size_t)bb * k + c];
+        const double v = ((dac + dbc) - dab) * 0.5;
+        R[c] = ((R[c] - dac) - dbc) + v;
         D[(size_t)ba * k + c] = v;
         D[(size_t)c * k + ba] = v;
       }
+      R[ba] = ru;
     }
     const int lo_a = id[ba] < id[bb];
     merges[2 * t] = lo_a ? id[ba] : id[bb];

@@ -18,10 +18,11 @@
 // only rows whose minimum pointed at a or b, or that now see a smaller value
 // at a, change; those pointing at a or b (usually few) are rescanned.
 //
-// Neighbour joining recomputes every live row's sum R(i) (one thread per
-// row, adding in increasing j as the sequential algorithm does) and every
-// pair's Q(a, b) = (r - 2) d(a, b) - R(a) - R(b) per step, so a step is
-// O(k^2) and the tree O(k^3); the FP64 rate bounds it.
+// Neighbour joining sums every row once (one thread per row, in increasing
+// j as the sequential algorithm does), then keeps the sums by the update
+// R(c) -= d(a, c) + d(b, c) - d(u, c) of each join; per step it recomputes
+// every live pair's Q(a, b) = (r - 2) d(a, b) - R(a) - R(b), one CTA per
+// live row, so a step is O(k^2) reads of the matrix and the tree O(k^3).
 #include <algorithm>
 #include <cmath>
 
@@ -196,11 +197,13 @@ __global__ void k_up_init(Upgma U) {
 struct Nj {
   double *D;        // k x k, symmetric
   double *R;        // per live slot: the sum of its distances to the other live slots
-  double *rq;       // per row i: smallest Q(i, j) over live j > i
+  double *rq;       // per live row i: smallest Q(i, j) over live j > i
   int32_t *rj;      // its j (-1: none)
   int32_t *n;       // cluster sizes per slot
   int32_t *id;      // cluster id per slot
   uint8_t *live;
+  int32_t *list;    // the live slots, in no particular order (r of them at step k - r)
+  int32_t *pos;     // a live slot's place in list
   int32_t *ctl;     // [0] a, [1] b, [2] an infinite distance seen
   double *dab;      // d(a, b) of the step
   int32_t *merges;
@@ -211,7 +214,7 @@ struct Nj {
 
 __global__ void k_nj_init(Nj J) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < J.k) { J.n[i] = 1; J.id[i] = i; J.live[i] = 1; }
+  if (i < J.k) { J.n[i] = 1; J.id[i] = i; J.live[i] = 1; J.list[i] = i; J.pos[i] = i; }
   if (i == 0) { J.ctl[0] = -1; J.ctl[1] = -1; J.ctl[2] = 0; }
 }
 
@@ -222,14 +225,14 @@ __global__ void k_nj_check(Nj J) {
     if (isinf(J.D[x])) J.ctl[2] = 1;
 }
 
-// R(i) over live j != i in increasing j (thread i reads column i: coalesced
-// across threads, and equal to row i since D is exactly symmetric)
+// the first row sums, R(i) over j != i in increasing j (thread i reads column
+// i: coalesced across threads, and equal to row i since D is exactly symmetric)
 __global__ void k_nj_rsum(Nj J) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= J.k || !J.live[i]) return;
+  if (i >= J.k) return;
   double s = 0.0;
   for (int32_t j = 0; j < J.k; ++j)
-    if (J.live[j] && j != i) s = __dadd_rn(s, J.D[(int64_t)j * J.k + i]);
+    if (j != i) s = __dadd_rn(s, J.D[(int64_t)j * J.k + i]);
   J.R[i] = s;
 }
 
@@ -239,15 +242,11 @@ __device__ __forceinline__ bool q_lt(double v1, int32_t j1, double v2, int32_t j
   return v1 < v2 || (v1 == v2 && j1 < j2);
 }
 
-// row i: the smallest (Q(i, j), j) over live j > i, one CTA per row
+// live row list[blockIdx.x]: the smallest (Q(i, j), j) over live j > i
 __global__ void k_nj_qrow(Nj J, double rm2) {
   __shared__ double sv[32];
   __shared__ int32_t sj[32];
-  const int32_t i = blockIdx.x;
-  if (!J.live[i]) {
-    if (threadIdx.x == 0) J.rj[i] = -1;
-    return;
-  }
+  const int32_t i = J.list[blockIdx.x];
   const double Ri = J.R[i];
   const double *row = J.D + (int64_t)i * J.k;
   double bv = 0.0;
@@ -273,23 +272,20 @@ __global__ void k_nj_qrow(Nj J, double rm2) {
   }
 }
 
-// record step t: the pair (a, b) with the smallest (Q, a, b) (or, with two
-// clusters left, the two), its branch lengths, and slot a takes the new cluster
+// record step t (r clusters live): the pair (a, b) with the smallest
+// (Q, a, b) (or, with two clusters left, the two), its branch lengths and
+// R(u); slot a takes the new cluster, b leaves the live list
 __global__ void k_nj_pick(Nj J, int32_t t, int32_t r) {
   __shared__ double sv[32];
   __shared__ int32_t sa[32], sb[32];
   double bv = 0.0;
   int32_t ba = -1, bb = -1;
-  if (r > 2) {
-    for (int32_t i = threadIdx.x; i < J.k; i += blockDim.x) {
-      const int32_t j = J.live[i] ? J.rj[i] : -1;
-      if (j < 0) continue;
-      const double v = J.rq[i];
-      if (ba < 0 || v < bv || (v == bv && (i < ba || (i == ba && j < bb)))) { bv = v; ba = i; bb = j; }
-    }
-  } else {
-    for (int32_t i = threadIdx.x; i < J.k; i += blockDim.x)
-      if (J.live[i] && (ba < 0 || i < ba)) { ba = i; bb = 0; }  // the lowest live slot per thread
+  for (int32_t p = threadIdx.x; p < r; p += blockDim.x) {
+    const int32_t i = J.list[p];
+    const int32_t j = r > 2 ? J.rj[i] : 0;  // with two left, the lower slot wins
+    if (j < 0) continue;
+    const double v = r > 2 ? J.rq[i] : 0.0;
+    if (ba < 0 || v < bv || (v == bv && (i < ba || (i == ba && j < bb)))) { bv = v; ba = i; bb = j; }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = 16; d > 0; d >>= 1) {
@@ -311,10 +307,9 @@ __global__ void k_nj_pick(Nj J, int32_t t, int32_t r) {
     da = __dadd_rn(__dmul_rn(dab, 0.5), __ddiv_rn(__dsub_rn(J.R[ba], J.R[bb]), (double)(2 * (r - 2))));
     db = __dsub_rn(dab, da);
     *J.dab = dab;
+    J.R[ba] = __dmul_rn(__dsub_rn(__dadd_rn(J.R[ba], J.R[bb]), __dmul_rn((double)r, dab)), 0.5);
   } else {
-    bb = -1;  // the other live slot: the first above ba
-    for (int32_t i = ba + 1; i < J.k && bb < 0; ++i)
-      if (J.live[i]) bb = i;
+    bb = J.list[0] == ba ? J.list[1] : J.list[0];  // the other live slot
     da = __dmul_rn(J.D[(int64_t)ba * J.k + bb], 0.5);
     db = da;
   }
@@ -328,22 +323,28 @@ __global__ void k_nj_pick(Nj J, int32_t t, int32_t r) {
   J.sizes[t] = J.n[ba];
   J.id[ba] = J.k + t;
   J.live[bb] = 0;
+  const int32_t p = J.pos[bb], last = J.list[r - 1];
+  J.list[p] = last;
+  J.pos[last] = p;
   J.ctl[0] = ba;
   J.ctl[1] = bb;
 }
 
-// row and column a of the new cluster: d(a, c) = (d(a, c) + d(b, c) - d(a, b)) / 2
-__global__ void k_nj_merge(Nj J) {
+// row and column a of the new cluster and the other live rows' sums:
+// d(a, c) = (d(a, c) + d(b, c) - d(a, b)) / 2, R(c) = R(c) - d(a, c) - d(b, c) + d(u, c)
+__global__ void k_nj_merge(Nj J, int32_t nlive) {
   const int32_t a = J.ctl[0], b = J.ctl[1];
   const double dab = *J.dab;
-  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < J.k; c += gridDim.x * blockDim.x) {
-    if (!J.live[c] || c == a || c == b) continue;
-    const double v = __dmul_rn(__dsub_rn(__dadd_rn(J.D[(int64_t)a * J.k + c], J.D[(int64_t)b * J.k + c]), dab), 0.5);
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nlive; p += gridDim.x * blockDim.x) {
+    const int32_t c = J.list[p];
+    if (c == a) continue;
+    const double dac = J.D[(int64_t)a * J.k + c], dbc = J.D[(int64_t)b * J.k + c];
+    const double v = __dmul_rn(__dsub_rn(__dadd_rn(dac, dbc), dab), 0.5);
+    J.R[c] = __dadd_rn(__dsub_rn(__dsub_rn(J.R[c], dac), dbc), v);
     J.D[(int64_t)a * J.k + c] = v;
     J.D[(int64_t)c * J.k + a] = v;
   }
 }
-
 }  // namespace
 
 // all pairs' LCS in caller labels (the i < j triangle), then the k x k distances
@@ -460,6 +461,8 @@ extern "C" int famsa_nj_tree(const famsa_family *fh, int32_t *merges, double *le
   J.n = sc.get<int32_t>(k);
   J.id = sc.get<int32_t>(k);
   J.live = sc.get<uint8_t>(k);
+  J.list = sc.get<int32_t>(k);
+  J.pos = sc.get<int32_t>(k);
   J.ctl = sc.get<int32_t>(3);
   J.dab = sc.get<double>(1);
   int32_t *d_iota = sc.get<int32_t>(k);
@@ -477,16 +480,12 @@ extern "C" int famsa_nj_tree(const famsa_family *fh, int32_t *merges, double *le
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   }
   if (err == cudaSuccess && !inf) {
-    const unsigned nr = (unsigned)((k + 63) / 64);
-    const unsigned nm = std::min<unsigned>((unsigned)((k + 255) / 256), 152);
+    k_nj_rsum<<<(unsigned)((k + 63) / 64), 64, 0, st>>>(J);
     for (int32_t t = 0; t + 1 < k && err == cudaSuccess; ++t) {
-      const int32_t r = k - t;
-      if (r > 2) {
-        k_nj_rsum<<<nr, 64, 0, st>>>(J);
-        k_nj_qrow<<<(unsigned)k, 256, 0, st>>>(J, (double)(r - 2));
-      }
+      const int32_t r = k - t;  // live clusters
+      if (r > 2) k_nj_qrow<<<(unsigned)r, 256, 0, st>>>(J, (double)(r - 2));
       k_nj_pick<<<1, 1024, 0, st>>>(J, t, r);
-      if (r > 2) k_nj_merge<<<nm, 256, 0, st>>>(J);
+      if (r > 2) k_nj_merge<<<std::min<unsigned>((unsigned)((r + 254) / 255), 152), 256, 0, st>>>(J, r - 1);
       if ((t & 1023) == 0) err = cudaGetLastError();
     }
     if (err == cudaSuccess) err = cudaGetLastError();
