@@ -326,9 +326,9 @@ __global__ void k_msf_gaps(int32_t n, const int32_t *gi, const uint64_t *ek, uin
 // The joins in increasing order: a union-find (union by size) whose roots
 // carry the head and tail of their leaf list.  At a join of x and y the list
 // of x is followed by the list of y, and the index of the joining edge is
-// recorded after the tail of x (gidx).  The walk from the final head gives
-// the leaf order and, per position, the edge whose height is its gap to the
-// next position.
+// recorded after the tail of x (gidx).  The final list (ranked in parallel,
+// below) gives the leaf order and, per position, the edge whose height is
+// its gap to the next position.
 //
 // The joins are sequential, so one thread commits them; the finds are not:
 // the 32 lanes of warp 0 look up the roots of the next 32 edges' endpoints
@@ -357,7 +357,6 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
     return;
   }
   const int lane = threadIdx.x & 31;
-  int32_t root = 0;
   for (int32_t c0 = 0; c0 < k - 1; c0 += kKrtChunk) {
     const int32_t cn = min(kKrtChunk, k - 1 - c0);
     for (int32_t j = threadIdx.x; j < cn; j += kKrtThreads) {
@@ -389,9 +388,9 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
             gidx[tx] = c0 + jb + l;
             nxt[tx] = hy;
             if (sxz < syz) {
-              par[x] = (I)y; size[y] = (I)(sxz + syz); head[y] = hx; root = y;
+              par[x] = (I)y; size[y] = (I)(sxz + syz); head[y] = hx;
             } else {
-              par[y] = (I)x; size[x] = (I)(sxz + syz); tail[x] = ty; root = x;
+              par[y] = (I)x; size[x] = (I)(sxz + syz); tail[x] = ty;
             }
           }
         }
@@ -408,13 +407,33 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
     }
     return;
   }
-  if (threadIdx.x == 0) {
-    int32_t v = head[root];
-    for (int32_t p = 0; p < k; ++p) {
-      ord[p] = v;
-      if (p + 1 < k) gi[p] = gidx[v];
-      v = nxt[v];
+  // The joined list runs from the root's head through nxt to an element that
+  // points to itself.  Its order comes from list ranking by pointer jumping
+  // (Wyllie): every element's distance to the end, ceil(log2 k) rounds of
+  // d(v) += d(J(v)), J(v) = J(J(v)), in the arrays the joins no longer need.
+  // (One thread walking the list took 5 ms at k = 20,000, most of it waiting
+  // on a global load per element.)
+  I *J0 = par, *D0 = size, *J1 = tail, *D1 = head;
+  for (int32_t v = threadIdx.x; v < k; v += kKrtThreads) {
+    const I nv = nxt[v];
+    J0[v] = nv;
+    D0[v] = (I)((int32_t)nv == v ? 0 : 1);
+  }
+  __syncthreads();
+  for (int32_t span = 1; span < k; span *= 2) {
+    for (int32_t v = threadIdx.x; v < k; v += kKrtThreads) {
+      const int32_t j = (int32_t)J0[v];
+      J1[v] = J0[j];
+      D1[v] = (I)((int32_t)D0[v] + (int32_t)D0[j]);
     }
+    __syncthreads();
+    I *t = J0; J0 = J1; J1 = t;
+    t = D0; D0 = D1; D1 = t;
+  }
+  for (int32_t v = threadIdx.x; v < k; v += kKrtThreads) {
+    const int32_t p = k - 1 - (int32_t)D0[v];
+    ord[p] = v;
+    if (p + 1 < k) gi[p] = gidx[v];
   }
 }
 
