@@ -30,6 +30,20 @@ int famsa_debug_peq(const famsa_family *f, uint32_t *peq, int64_t *word_off, int
  * use it to check that a call allocates nothing. */
 int64_t famsa_debug_alloc_count(void);
 
+/* The checked build (libfamsa_gpu_checked.so, compiled with -DFAMSA_CHECKED)
+ * tests the invariants each kernel's indexing relies on (indices inside their
+ * buffers, rows inside their kernel's width, ids inside their range) and
+ * counts every failure, skipping the access it guards, instead of faulting.
+ * Returns the failures counted so far on the current device, with the source
+ * line of the first one in *first_line (may be NULL); -1 from the normal
+ * build, which has no checks. */
+int64_t famsa_debug_check_count(int64_t *first_line);
+
+/* The checker's own test: in the checked build, launches one kernel whose one
+ * check fails on purpose (it guards no access), so the count above grows by
+ * one; returns FAMSA_OK (or ECUDA).  -1 from the normal build. */
+int famsa_debug_check_selftest(void);
+
 /* Rows wider than w 64-bit words do not use the thread-per-pair LCS kernel
  * (default 32, the thread-per-pair maximum): they take the sliced kernel
  * where famsa_debug_set_slices covers their width, else warp-per-pair (with

@@ -22,7 +22,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfamsa_gpu.so")
+# FAMSA_CHECKED=1 selects the checked build (kernels count failed invariants;
+# python -m paper_1603_06958_gb300.build --checked)
+LIB_PATH = os.path.join(_HERE, "libfamsa_gpu_checked.so" if os.environ.get("FAMSA_CHECKED") == "1"
+                        else "libfamsa_gpu.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 HEADERS = [os.path.join(INCLUDE, h) for h in ("famsa_gpu.h", "famsa_gpu_debug.h")]
 
@@ -59,7 +62,8 @@ def load(path: str = LIB_PATH):
         if _lib is not None:
             return _lib
         if not os.path.exists(path):
-            raise ImportError("libfamsa_gpu.so not built: run python -m paper_1603_06958_gb300.build")
+            raise ImportError("%s not built: run python -m paper_1603_06958_gb300.build%s"
+                              % (os.path.basename(path), " --checked" if "checked" in path else ""))
         lib = ctypes.CDLL(path)
         i32, u64p = ctypes.c_int32, _P
         sig = {
@@ -100,6 +104,8 @@ def load(path: str = LIB_PATH):
             "famsa_debug_set_row_block": ([ctypes.c_int], ctypes.c_int),
             "famsa_debug_alloc_count": ([], ctypes.c_int64),
             "famsa_debug_set_slices": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "famsa_debug_check_count": ([_P], ctypes.c_int64),
+            "famsa_debug_check_selftest": ([], ctypes.c_int),
             "famsa_debug_peq": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "famsa_merge_similarity": ([_P, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
             "famsa_msf_rows": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, _P],
@@ -776,6 +782,19 @@ def debug_peq(fam: Family) -> dict:
     _check(load().famsa_debug_peq(fam.handle, peq.ctypes.data, off.ctypes.data, perm.ctypes.data, None),
            "famsa_debug_peq")
     return {"peq": peq, "word_off": off, "perm": perm}
+
+
+def debug_check_count():
+    """(failed kernel checks so far, source line of the first) from the checked
+    build; (-1, 0) from the normal one."""
+    line = ctypes.c_int64()
+    n = load().famsa_debug_check_count(ctypes.byref(line))
+    return int(n), int(line.value)
+
+
+def debug_check_selftest() -> int:
+    """Checked build: one kernel check fails on purpose (the count grows by one)."""
+    return int(load().famsa_debug_check_selftest())
 
 
 def debug_alloc_count() -> int:

@@ -1,6 +1,12 @@
 """Build libfamsa_gpu.so in-tree for sm_103a (nvcc, parallel translation units).
 
-Usage: python -m paper_1603_06958_gb300.build [--force]
+With --checked (or build(checked=True)) it also builds
+libfamsa_gpu_checked.so: the same sources with -DFAMSA_CHECKED, whose kernels
+count every failed invariant (an index outside its buffer, a row wider than
+its kernel) instead of trusting it.  The binding loads that library when
+FAMSA_CHECKED=1 is set in the environment.
+
+Usage: python -m paper_1603_06958_gb300.build [--force] [--checked]
 """
 from __future__ import annotations
 
@@ -13,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfamsa_gpu.so")
+OBJ_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libfamsa_gpu_checked.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "pack.cu", "lcs.cu", "lcs_tpp_a.cu", "lcs_tpp_b.cu", "lcs_tpp_c.cu", "lcs_tpp_d.cu",
@@ -51,17 +59,17 @@ def _gen_step():
         os.replace(inc + ".tmp", inc)
 
 
-def _build_lib(sources, lib, force, verbose, ptxas_v):
-    os.makedirs(OBJ, exist_ok=True)
+def _build_lib(sources, lib, force, verbose, ptxas_v, obj_dir=OBJ, extra=()):
+    os.makedirs(obj_dir, exist_ok=True)
     hdr = max(_mtime(h if os.path.isabs(h) else os.path.join(CSRC, h)) for h in HEADERS)
     jobs = []
     objs = []
     for s in sources:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OBJ, s.replace("/", "_").replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, s.replace("/", "_").replace(".cu", ".o"))
         objs.append(obj)
         if force or _mtime(obj) < max(_mtime(src), hdr):
-            cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_v else []) + \
+            cmd = [nvcc()] + ARCH + FLAGS + list(extra) + (["-Xptxas", "-v"] if ptxas_v else []) + \
                 ["-c", src, "-o", obj]
             jobs.append(cmd)
     if jobs:
@@ -81,13 +89,17 @@ def _build_lib(sources, lib, force, verbose, ptxas_v):
     return lib
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    """Build libfamsa_gpu.so (and the benchmark's probe library beside it)."""
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, checked: bool = False) -> str:
+    """Build libfamsa_gpu.so (and the benchmark's probe library beside it);
+    with checked=True also libfamsa_gpu_checked.so."""
     _gen_step()
     _build_lib(SOURCES, LIB, force, verbose, ptxas_v)
     _build_lib(PROBE_SOURCES, PROBE_LIB, force, verbose, ptxas_v)
+    if checked:
+        _build_lib(SOURCES, LIB_CHECKED, force, verbose, ptxas_v, OBJ_CHECKED, ["-DFAMSA_CHECKED"])
     return LIB
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv)
+    build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv,
+          checked="--checked" in sys.argv)

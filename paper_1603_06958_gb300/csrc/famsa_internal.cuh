@@ -163,4 +163,36 @@ int slink_tree(Family *f, int32_t *pi, uint64_t *lambda_num, uint32_t *lambda_de
 
 int status_from_cuda(cudaError_t e);
 
+// ------------------------------------------------------------ checked build
+// Built with -DFAMSA_CHECKED (libfamsa_gpu_checked.so), kernels test the
+// invariants their indexing relies on -- every index inside its buffer, every
+// row inside its kernel's width, every component id inside its range -- and
+// count each failure instead of trusting it; a failed check skips the access
+// it guards.  It stands in for a memory checker.  The normal build compiles
+// every check to nothing.  Each translation unit keeps its own counters
+// (count, line of the first failure), read through famsa_debug_check_count.
+using CheckReader = void (*)(unsigned long long *count_and_line);
+int register_check_reader(CheckReader r);
+void read_checks(unsigned long long *count, unsigned long long *first_line);
+
 }  // namespace famsa
+
+#ifdef FAMSA_CHECKED
+namespace {
+__device__ unsigned long long g_check_fail[2];  // failures, line of the first one
+__device__ __forceinline__ bool famsa_expect(bool ok, int line) {
+  if (!ok) {
+    atomicAdd(&g_check_fail[0], 1ull);
+    atomicCAS(&g_check_fail[1], 0ull, (unsigned long long)line);
+  }
+  return ok;
+}
+void read_checks_here(unsigned long long *v) {
+  if (cudaMemcpyFromSymbol(v, g_check_fail, sizeof(g_check_fail)) != cudaSuccess) v[0] = v[1] = 0;
+}
+const int g_check_registered = famsa::register_check_reader(read_checks_here);
+}  // namespace
+#define FAMSA_EXPECT(cond) famsa_expect((cond), __LINE__)
+#else
+#define FAMSA_EXPECT(cond) true
+#endif

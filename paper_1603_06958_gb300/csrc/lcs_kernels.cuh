@@ -65,28 +65,30 @@ __device__ __forceinline__ void emit_lcs(const KParams &p, int32_t e, int32_t ri
       if (t >= rid) return;
       int64_t a = p.col_perm[t], b = p.col_perm[rid];
       int64_t i = a < b ? a : b, j = a < b ? b : a;
-      static_cast<int32_t *>(p.out)[tri_index(i, j, p.k)] = L;
+      if (FAMSA_EXPECT(i >= 0 && j < p.k && i != j)) static_cast<int32_t *>(p.out)[tri_index(i, j, p.k)] = L;
       return;
     }
     case kOutRowsOrig: {
       int64_t oc = p.col_perm[t], orr = p.row_orig[e];
       if (oc >= orr) return;
       int64_t base = (orr * (orr - 1) - (int64_t)p.row0 * (p.row0 - 1)) / 2;
-      static_cast<int32_t *>(p.out)[base + oc] = L;
+      if (FAMSA_EXPECT(oc >= 0 && orr >= p.row0 && orr < p.k)) static_cast<int32_t *>(p.out)[base + oc] = L;
       return;
     }
     case kOutRowbuf: {
       if (t >= rid) return;
-      static_cast<uint16_t *>(p.out)[(int64_t)(rid - p.row0) * p.ld + t] = (uint16_t)L;
+      if (FAMSA_EXPECT(rid >= p.row0 && t < p.ld))
+        static_cast<uint16_t *>(p.out)[(int64_t)(rid - p.row0) * p.ld + t] = (uint16_t)L;
       return;
     }
     case kOutBatch: {
       if (t >= rid) return;
-      static_cast<uint16_t *>(p.out)[p.row_base[e] + t] = (uint16_t)L;
+      if (FAMSA_EXPECT(p.row_base[e] + t >= 0)) static_cast<uint16_t *>(p.out)[p.row_base[e] + t] = (uint16_t)L;
       return;
     }
     default: {  // kOutQuery
-      static_cast<int32_t *>(p.out)[(int64_t)rid * p.ld + p.col_perm[t]] = L;
+      const int32_t c = p.col_perm[t];
+      if (FAMSA_EXPECT(rid >= 0 && c >= 0 && c < p.ld)) static_cast<int32_t *>(p.out)[(int64_t)rid * p.ld + c] = L;
       return;
     }
   }
@@ -120,6 +122,8 @@ __global__ void __launch_bounds__(kTppThreads, 1) k_lcs_tpp(KParams p) {
   if (gbase * kGroup >= col_limit) return;
 
   // stage the tile's Peq planes; rows shorter than W words are zero-padded
+  if (threadIdx.x < R && tile_e + (int32_t)threadIdx.x < tile_end)
+    (void)FAMSA_EXPECT((p.row_len[tile_e + threadIdx.x] + 63) / 64 <= W);  // a wider row would be cut
   for (int i = threadIdx.x; i < R * W * 16; i += kTppThreads) {
     int r = i / (W * 16), rem = i - r * (W * 16), w = rem >> 4;
     int32_t e = tile_e + r;
@@ -217,6 +221,7 @@ __global__ void __launch_bounds__(32 * kSliceMaxG, 1) k_lcs_slice(KParams p) {
   const int32_t col_limit = p.triangle ? rid : p.n_cols;
   if (grp >= p.n_groups || grp * kGroup >= col_limit) return;  // uniform over the CTA
   const int32_t Wr = (p.row_len[e] + 63) / 64;
+  if (threadIdx.x == 0) (void)FAMSA_EXPECT(Wr <= G * WL && G <= kSliceMaxG && (int)blockDim.x == 32 * G);
   uint32_t *sPeq = sSl;                               // G * WL words x 64 u32
   uint32_t *sMask = sSl + G * WL * kPeqWordU32;       // [2][G][32] carry masks
   uint32_t *sSum = sMask + 2 * G * kGroup;            // [G][32] partial counts
@@ -302,6 +307,7 @@ __global__ void __launch_bounds__(kWppThreads) k_lcs_wpp(KParams p) {
   }
   const int32_t rid = p.row_id[e];
   const int32_t Wr = (p.row_len[e] + 63) / 64;
+  if (threadIdx.x == 0) (void)FAMSA_EXPECT(Wr <= WP);
   const int32_t col_limit = p.triangle ? rid : p.n_cols;
   if (c_begin >= col_limit) return;
   const int32_t c_end = min(c_begin + kWppCols, col_limit);

@@ -46,6 +46,28 @@ int status_from_cuda(cudaError_t e) {
   return FAMSA_ECUDA;
 }
 
+// one reader per translation unit of the checked build (none in the normal one)
+static std::vector<CheckReader> &check_readers() {
+  static std::vector<CheckReader> r;
+  return r;
+}
+
+int register_check_reader(CheckReader r) {
+  check_readers().push_back(r);
+  return 1;
+}
+
+void read_checks(unsigned long long *count, unsigned long long *first_line) {
+  *count = 0;
+  *first_line = 0;
+  for (CheckReader r : check_readers()) {
+    unsigned long long v[2] = {0, 0};
+    r(v);
+    *count += v[0];
+    if (!*first_line && v[1]) *first_line = v[1];
+  }
+}
+
 // ----------------------------------------------------------------- kernels
 
 __global__ void k_lengths(const int64_t *off, int32_t k, int64_t base, int32_t *len,
@@ -174,6 +196,8 @@ __global__ void k_pack_peq(const uint8_t *res, const int64_t *off, const int32_t
   const uint8_t *a = res + off[idx];
   int32_t len = (int32_t)(off[idx + 1] - off[idx]);
   int32_t W = (len + 63) / 64;
+  // the sequence's words are exactly its slot's share of the table
+  if (!FAMSA_EXPECT(len >= 1 && peq_off[s + 1] - peq_off[s] == W)) return;
   uint32_t *dst = peq + peq_off[s] * kPeqWordU32;
   for (int32_t w = 0; w < W; ++w) {
     int32_t p0 = w * 64 + lane, p1 = p0 + 32;
@@ -203,6 +227,8 @@ __global__ void k_col_layout(const uint8_t *res, const int64_t *off, const int32
     int32_t s = g * kGroup + lane;
     uint32_t w[4];
     int32_t len = s < k ? slen[s] : 0;
+    // a slot's residues fit its group's chunks, and its label is a sequence
+    if (len > 0 && !FAMSA_EXPECT(len <= nch * kChunk && perm[s] >= 0)) len = 0;
     const uint8_t *a = len > 0 ? res + off[perm[s]] : res;  // pad slots have length 0
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -439,6 +465,32 @@ extern "C" int famsa_debug_fail_alloc_after(int n) {
 }
 
 extern "C" int64_t famsa_debug_alloc_count(void) { return famsa::g_alloc_count.load(); }
+
+// one check that fails on purpose and guards nothing: the checker's own test
+__global__ void k_check_selftest() { (void)FAMSA_EXPECT(threadIdx.x != 0); }
+
+extern "C" int famsa_debug_check_selftest(void) {
+#ifdef FAMSA_CHECKED
+  k_check_selftest<<<1, 1>>>();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return famsa::status_from_cuda(e);
+#else
+  return -1;
+#endif
+}
+
+extern "C" int64_t famsa_debug_check_count(int64_t *first_line) {
+#ifdef FAMSA_CHECKED
+  unsigned long long n = 0, line = 0;
+  famsa::read_checks(&n, &line);
+  if (first_line) *first_line = (int64_t)line;
+  return (int64_t)n;
+#else
+  if (first_line) *first_line = 0;
+  return -1;
+#endif
+}
 
 // The packed match-bitmask tables of a family, for tests: peq (words x 64
 // u32, host) in the family's (length, index) order, the first word of each

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kRowThreads) k_msf_rowmin(MsfState S, const ui
   int32_t bo = INT32_MAX;
   const uint32_t lq = kFirst ? (uint32_t)S.slen[q] : 0;
 #pragma unroll 4
+  if (threadIdx.x == 0) (void)FAMSA_EXPECT(q < r1 && q <= ld && cq >= 0 && cq < r1);
   for (int32_t t = threadIdx.x; t < q; t += kRowThreads) {
     uint64_t key;
     if (kFirst) {
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kColX * kColY) k_msf_colmin(MsfState S, int64_
     const int32_t qb = max(r0, t + 1);
 #pragma unroll 4
     for (int32_t q = qb + ty; q < r1; q += kColY) {
-      if (S.comp[q] != ct) {
+      if (FAMSA_EXPECT(t < ld) && S.comp[q] != ct) {
         const uint64_t key = S.keys[(int64_t)(q - r0) * ld + t];
         if (key < bk) { bk = key; bo = q; }  // q ascends per thread
       }
@@ -184,6 +185,7 @@ __global__ void k_msf_cmin(MsfState S, int32_t r0, int32_t r1, int32_t m) {
       ab = S.vab[v];
     }
     if (key != kMsfNone) c = S.comp[v];
+    if (!FAMSA_EXPECT(c < r1)) c = -1;
   }
   // warp-aggregated atomics: lanes of one component reduce first
   const unsigned grp = __match_any_sync(0xffffffffu, c);
@@ -203,8 +205,9 @@ __global__ void k_msf_cmin(MsfState S, int32_t r0, int32_t r1, int32_t m) {
   if (i >= r1 && i < (int64_t)r1 + m) {
     const int32_t e = (int32_t)(i - r1);
     const int32_t a = S.ma[e], b = S.mb[e];
-    const int32_t ca = S.comp[a], cb = S.comp[b];
-    if (ca != cb) {
+    const bool in = FAMSA_EXPECT(a >= 0 && a < r1 && b >= 0 && b < r1);
+    const int32_t ca = in ? S.comp[a] : 0, cb = in ? S.comp[b] : 0;
+    if (ca != cb && FAMSA_EXPECT(ca >= 0 && ca < r1 && cb >= 0 && cb < r1)) {
       const uint64_t ek = S.mkey[e];
       if (!kPhaseB) {
         if (ek < S.bkey[ca]) atomicMin((unsigned long long *)&S.bkey[ca], ek);
@@ -232,8 +235,16 @@ __global__ void k_msf_hook(MsfState S, int32_t r1) {
   }
   const uint64_t ab = S.bab[c];
   const int32_t a = (int32_t)(ab >> 32), b = (int32_t)(ab & 0xffffffffu);
+  if (!FAMSA_EXPECT(a >= 0 && a < r1 && b >= 0 && b < r1)) {
+    S.par[c] = c;
+    return;
+  }
   const int32_t ca = S.comp[a];
   const int32_t o = ca == c ? S.comp[b] : ca;
+  if (!FAMSA_EXPECT(o >= 0 && o < r1 && o != c)) {
+    S.par[c] = c;
+    return;
+  }
   const bool mutual = S.bkey[o] == bk && S.bab[o] == ab;
   S.par[c] = (mutual && c < o) ? c : o;
   if (!mutual || c < o) {
@@ -255,7 +266,8 @@ __global__ void k_msf_jump(MsfState S, int32_t r1) {
   const int32_t v = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (v < r1) {
     int32_t x = S.comp[v];
-    for (int32_t it = 0; it < r1 && S.par[x] != x; ++it) x = S.par[x];
+    for (int32_t it = 0; it < r1 && FAMSA_EXPECT(x >= 0 && x < r1) && S.par[x] != x; ++it) x = S.par[x];
+    (void)FAMSA_EXPECT(x >= 0 && x < r1 && S.par[x] == x);  // the walk ended at a root
     S.comp[v] = x;
     S.bkey[v] = kMsfNone;
     S.bab[v] = kMsfNone;
@@ -311,6 +323,7 @@ __global__ void k_msf_gather(int32_t n, const int32_t *order, const uint64_t *mk
   const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (i < n) {
     const int32_t e = order[i];
+    if (!FAMSA_EXPECT(e >= 0 && e < n)) return;
     ek[i] = mkey[e];
     ea[i] = ma[e];
     eb[i] = mb[e];
@@ -320,7 +333,7 @@ __global__ void k_msf_gather(int32_t n, const int32_t *order, const uint64_t *mk
 // gap p = the height of the join recorded after position p
 __global__ void k_msf_gaps(int32_t n, const int32_t *gi, const uint64_t *ek, uint64_t *gap) {
   const int32_t p = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-  if (p < n) gap[p] = gap_code(ek[gi[p]]);
+  if (p < n && FAMSA_EXPECT(gi[p] >= 0 && gi[p] < n)) gap[p] = gap_code(ek[gi[p]]);
 }
 
 // The joins in increasing order: a union-find (union by size) whose roots
