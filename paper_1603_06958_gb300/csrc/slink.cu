@@ -182,15 +182,18 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
     }
     int32_t blk = 0;
     // the first block is an eighth of the others: the row update can start
-    // once its few, short rows are done
-    const int32_t B0 = g_row_block ? B : std::min(B, std::max(B / 8, 64));  // the buffers hold B rows
+    // once its few, short rows are done.  A family of up to 2,048 points is
+    // one block (B = k - 1): its whole LCS is short, and one set of tree
+    // rounds (about 55 launches) costs less than overlapping three.
+    const bool one_block = msf && !g_row_block && k <= 2048;
+    const int32_t B0 = g_row_block || one_block ? B : std::min(B, std::max(B / 8, 64));  // the buffers hold B rows
     for (int32_t r0 = 1, r1 = 0; r0 < k; r0 = r1, ++blk) {
       {
         // the last block is a quarter of the others, so that little row
         // update work is left once the last LCS block is done
         int32_t take = blk == 0 ? B0 : B;
         const int32_t rem = k - r0, tail_rows = std::max(B / 4, 1);
-        if (msf && !g_row_block && rem > tail_rows && rem <= take + tail_rows) take = rem - tail_rows;
+        if (msf && !g_row_block && !one_block && rem > tail_rows && rem <= take + tail_rows) take = rem - tail_rows;
         r1 = std::min(r0 + take, k);
       }
       const int buf = blk % kRowBuffers;
