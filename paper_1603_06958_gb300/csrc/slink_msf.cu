@@ -393,11 +393,19 @@ __device__ __forceinline__ void krt_run(int32_t k, const int32_t *ea, const int3
           const int32_t nb = min(32, cn - jb);
           for (int32_t l = 0; l < nb; ++l) {
             int32_t x = sx[l], y = sy[l];
-            while ((int32_t)par[x] != x) x = par[x];  // links added by the joins since the lookup
-            while ((int32_t)par[y] != y) y = par[y];
+            // the looked-up roots usually still are roots: read their records
+            // and the root test at once, and walk (then re-read) only when a
+            // join since the lookup moved one
+            I px = par[x], py = par[y];
+            I tx = tail[x], hy = head[y], hx = head[x], ty = tail[y];
+            I sxz = size[x], syz = size[y];
+            if ((int32_t)px != x || (int32_t)py != y) {
+              while ((int32_t)par[x] != x) x = par[x];
+              while ((int32_t)par[y] != y) y = par[y];
+              tx = tail[x]; hy = head[y]; hx = head[x]; ty = tail[y];
+              sxz = size[x]; syz = size[y];
+            }
             if (x == y) { *err |= 4; break; }  // two points already joined: not a tree
-            const I tx = tail[x], hy = head[y], hx = head[x], ty = tail[y];
-            const I sxz = size[x], syz = size[y];
             gidx[tx] = c0 + jb + l;
             nxt[tx] = hy;
             if (sxz < syz) {
