@@ -242,31 +242,45 @@ __device__ __forceinline__ bool q_lt(double v1, int32_t j1, double v2, int32_t j
   return v1 < v2 || (v1 == v2 && j1 < j2);
 }
 
+// The order of finite doubles as unsigned integers: flip the sign bit of a
+// non-negative value and every bit of a negative one (the two zeros, equal as
+// doubles, share a key).  The scan below compares these on the integer ALU
+// instead of issuing a fourth FP64 instruction per pair.
+__device__ __forceinline__ uint64_t dkey(double q) {
+  uint64_t b = (uint64_t)__double_as_longlong(q);
+  if ((b << 1) == 0) b = 0;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // live row list[blockIdx.x]: the smallest (Q(i, j), j) over live j > i
 __global__ void k_nj_qrow(Nj J, double rm2) {
+  __shared__ uint64_t sk[32];
   __shared__ double sv[32];
   __shared__ int32_t sj[32];
   const int32_t i = J.list[blockIdx.x];
   const double Ri = J.R[i];
   const double *row = J.D + (int64_t)i * J.k;
+  uint64_t bk = ~0ull;
   double bv = 0.0;
   int32_t bj = -1;
   for (int32_t j = i + 1 + threadIdx.x; j < J.k; j += blockDim.x) {
     if (!J.live[j]) continue;
     const double q = __dsub_rn(__dsub_rn(__dmul_rn(rm2, row[j]), Ri), J.R[j]);
-    if (q_lt(q, j, bv, bj)) { bv = q; bj = j; }
+    const uint64_t kq = dkey(q);
+    if (kq < bk) { bk = kq; bv = q; bj = j; }  // j ascends per thread: the first minimum stays
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = 16; d > 0; d >>= 1) {
+    const uint64_t k2 = __shfl_down_sync(0xffffffffu, bk, d);
     const double v2 = __shfl_down_sync(0xffffffffu, bv, d);
     const int32_t j2 = __shfl_down_sync(0xffffffffu, bj, d);
-    if (q_lt(v2, j2, bv, bj)) { bv = v2; bj = j2; }
+    if (j2 >= 0 && (bj < 0 || k2 < bk || (k2 == bk && j2 < bj))) { bk = k2; bv = v2; bj = j2; }
   }
-  if (lane == 0) { sv[warp] = bv; sj[warp] = bj; }
+  if (lane == 0) { sk[warp] = bk; sv[warp] = bv; sj[warp] = bj; }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (q_lt(sv[w], sj[w], bv, bj)) { bv = sv[w]; bj = sj[w]; }
+      if (sj[w] >= 0 && (bj < 0 || sk[w] < bk || (sk[w] == bk && sj[w] < bj))) { bk = sk[w]; bv = sv[w]; bj = sj[w]; }
     J.rq[i] = bv;
     J.rj[i] = bj;
   }
