@@ -89,6 +89,7 @@ int famsa_encode_ascii(const char *text, int64_t n, uint8_t *codes, int64_t *bad
 
 int famsa_pack_peq(const uint8_t *residues, const int64_t *offsets, int32_t k,
                    int residues_on_device, void *cuda_stream, famsa_family **out) {
+  TraceRange trace("famsa_pack_peq");
   if (!out) return FAMSA_EINVAL;
   *out = nullptr;
   if (!residues || !offsets || k < 1) return FAMSA_EINVAL;
@@ -129,6 +130,7 @@ int famsa_last_stats(const famsa_family *fh, int64_t *stats) {
 
 int famsa_lcs_allpairs(const famsa_family *fh, int32_t *lcs_out, int out_on_device,
                        void *cuda_stream) {
+  TraceRange trace("famsa_lcs_allpairs");
   if (!fh || !lcs_out) return FAMSA_EINVAL;
   Family *f = const_cast<Family *>(reinterpret_cast<const Family *>(fh));
   std::lock_guard<std::mutex> lk(f->mu);
@@ -172,6 +174,7 @@ int famsa_lcs_allpairs(const famsa_family *fh, int32_t *lcs_out, int out_on_devi
 
 int famsa_lcs_rows(const famsa_family *fh, int32_t row_begin, int32_t row_end, int32_t *out,
                    int out_on_device, void *cuda_stream) {
+  TraceRange trace("famsa_lcs_rows");
   if (!fh) return FAMSA_EINVAL;
   Family *f = const_cast<Family *>(reinterpret_cast<const Family *>(fh));
   if (row_begin < 0 || row_end < row_begin || row_end > f->k) return FAMSA_EINVAL;
@@ -243,6 +246,7 @@ int famsa_lcs_rows(const famsa_family *fh, int32_t row_begin, int32_t row_end, i
 int famsa_lcs_query(const famsa_family *fh, const uint8_t *q, const int64_t *q_offsets,
                     int32_t nq, int q_on_device, int32_t *out, int out_on_device,
                     void *cuda_stream) {
+  TraceRange trace("famsa_lcs_query");
   if (!fh || !q || !q_offsets || !out || nq < 1) return FAMSA_EINVAL;
   Family *f = const_cast<Family *>(reinterpret_cast<const Family *>(fh));
   std::lock_guard<std::mutex> lk(f->mu);
@@ -336,6 +340,7 @@ int famsa_lcs_query(const famsa_family *fh, const uint8_t *q, const int64_t *q_o
 int famsa_slink_tree(const famsa_family *fh, int32_t *pi, uint64_t *lambda_num,
                      uint32_t *lambda_den, int32_t *merges, uint64_t *h_num, uint32_t *h_den,
                      int32_t *sizes, int out_on_device, void *cuda_stream) {
+  TraceRange trace("famsa_slink_tree");
   if (!fh) return FAMSA_EINVAL;
   Family *f = const_cast<Family *>(reinterpret_cast<const Family *>(fh));
   std::lock_guard<std::mutex> lk(f->mu);

@@ -932,6 +932,7 @@ int famsa_batch_pack(const uint8_t *residues, const int64_t *offsets, int64_t n_
   if (!out) return FAMSA_EINVAL;
   *out = nullptr;
   if (!residues || !offsets || !family_offsets) return FAMSA_EINVAL;
+  TraceRange trace("famsa_batch_pack");
   Batch *b = nullptr;
   int rc = batch_pack(residues, offsets, n_seqs, family_offsets, n_families, residues_on_device != 0,
                       (cudaStream_t)cuda_stream, &b);
@@ -947,7 +948,9 @@ int famsa_batch_tree(famsa_batch *bh, int32_t *pi, uint64_t *lambda_num, uint32_
   Batch *b = reinterpret_cast<Batch *>(bh);
   std::lock_guard<std::mutex> lk(b->mu);
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  TraceRange trace("famsa_batch_tree");
   if (!b->planned) {
+    TraceRange trace_plan("batch plan and graph capture");
     int rc = batch_plan(b, st);
     if (rc != FAMSA_OK) return rc;
   }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -162,6 +163,17 @@ int slink_tree(Family *f, int32_t *pi, uint64_t *lambda_num, uint32_t *lambda_de
                bool out_on_device, cudaStream_t st);
 
 int status_from_cuda(cudaError_t e);
+
+// An NVTX range for the lifetime of a scope: the entry points, each row
+// block of a tree build, a batch's plan and graph launch and each served
+// request show up by name on a profiler's timeline (nsys, ncu --nvtx).  With
+// no profiler attached a push or pop costs next to nothing.
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // ------------------------------------------------------------ checked build
 // Built with -DFAMSA_CHECKED (libfamsa_gpu_checked.so), kernels test the

@@ -138,6 +138,7 @@ static Request *pick(Server *s) {
 }
 
 static void run_request(Server *s, Request *r, cudaStream_t st) {
+  TraceRange trace(r->kind == 0 ? "served tree request" : "served query request");
   int rc = FAMSA_OK;
   if (r->kind == 0) {
     famsa_family *fam = nullptr;

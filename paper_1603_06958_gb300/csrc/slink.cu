@@ -13,6 +13,7 @@
 // order, and the outputs are produced in the caller's labels by the
 // finalisation.
 #include <algorithm>
+#include <cstdio>
 #include <vector>
 
 #include "slink_msf.cuh"
@@ -196,6 +197,9 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
         if (msf && !g_row_block && !one_block && rem > tail_rows && rem <= take + tail_rows) take = rem - tail_rows;
         r1 = std::min(r0 + take, k);
       }
+      char tname[64];
+      snprintf(tname, sizeof tname, "row block %d: rows %d-%d", blk, r0, r1 - 1);
+      TraceRange trace(tname);
       const int buf = blk % kRowBuffers;
       if (blk >= kRowBuffers) CKE(cudaStreamWaitEvent(sA, upd_done[buf], 0));
       if (g_serial && blk >= 1) CKE(cudaStreamWaitEvent(sA, upd_done[(blk - 1) % kRowBuffers], 0));
@@ -237,6 +241,7 @@ int slink_tree(Family *f, int32_t *pi_out, uint64_t *lnum_out, uint32_t *lden_ou
       CKE(cudaEventRecord(upd_done[buf], sB));
     }
     // finalisation from the layout of k points (buffer k & 1), keys in the wide packing
+    TraceRange trace_fin("leaf order and finalisation");
     CKE(timing_event(sB));
     // (the streamed lambda is widened for the debug export; the finalisation
     // widens the gaps itself)
